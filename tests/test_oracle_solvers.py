@@ -1,0 +1,167 @@
+"""Pins of the oracle's solvers: GMRES, successive approximations, the local
+Darcy and Stokes solves (Fig. 4 tests) and the Dirichlet-Neumann iteration
+against the Joseph-Tao porous sphere (Section 7.3, Tables 1-2)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from oracle import analytic as A
+from oracle import quadrature as Q
+from oracle import solvers as S
+
+
+def test_gmres_matches_dense_solve_with_restarts():
+    rng = np.random.default_rng(7)
+    n = 80
+    M = np.eye(n) * 3 + rng.normal(size=(n, n)) / math.sqrt(n)
+    b = rng.normal(size=n)
+    x, its, rel = S.gmres(lambda v: M @ v, b, tol=1e-12, restart=10, maxit=500)
+    assert rel <= 1e-12
+    assert np.linalg.norm(M @ x - b) / np.linalg.norm(b) < 1e-11
+    assert np.allclose(x, np.linalg.solve(M, b), rtol=0, atol=1e-10)
+    # full GMRES on an n-dimensional problem terminates within n steps
+    x2, its2, _ = S.gmres(lambda v: M @ v, b, tol=1e-13, restart=n, maxit=n)
+    assert its2 <= n and np.allclose(x2, np.linalg.solve(M, b), atol=1e-10)
+
+
+def test_successive_approximation_contraction():
+    rng = np.random.default_rng(1)
+    n = 30
+    C = rng.normal(size=(n, n))
+    C *= 0.5 / np.linalg.norm(C, 2)
+    b = rng.normal(size=n)
+    x, its, rel = S.successive_approx(lambda v: C @ v + b, np.zeros(n), tol=1e-13)
+    assert np.allclose(x, np.linalg.solve(np.eye(n) - C, b), atol=1e-11)
+
+
+def _darcy_fig4(h):
+    R, mu, kappa = 0.8, 1.0, 1.0
+    p = Q.sphere_points(R, h)
+    x, y, z = p["xyz"]
+    n = p["nrm"]
+    P = np.exp(x) * np.sin(y)
+    dP = np.exp(x) * (np.sin(y) * n[0] + np.cos(y) * n[1])
+    q = -(kappa / mu) * dP            # Darcy's law: u . n = -(kappa/mu) dp/dn
+    ps, its, rel = S.darcy_solve(p, 3 * h, mu, kappa, q, tol=1e-11)
+    return S.rms(ps - (P - S.weighted_mean(p, P))), its
+
+
+def _stokes_fig4(h):
+    # The continuous operator I/2 - K has the normal field n in its null
+    # space (K n = n/2); the discrete I - D^S inherits a near-null vector
+    # (eigenvalue O(h^5)), so the solve is compared modulo that mode.
+    p = Q.sphere_points(0.8, h)
+    u, sig = A.stokeslet(p["xyz"], [0.2, 0.0, 0.0], [1.0, 0.0, 0.0], 1.0)
+    f = np.einsum("ikn,kn->in", sig, p["nrm"])
+    us, its, rel = S.stokes_solve(p, 3 * h, 1.0, f, [0.0, 0.0, 0.0], tol=1e-11)
+    e = us - u
+    n = p["nrm"]
+    e = e - (e * n).sum() / (n * n).sum() * n
+    return S.rms(e), its
+
+
+def test_stokes_double_layer_normal_mode():
+    # K n = n/2 for the continuous operator, i.e. D^S n = n: a pin of the
+    # stresslet's sign, its normal contraction and the 6/(8 pi) factor
+    errs = []
+    for h in (1 / 8, 1 / 16):
+        p = Q.sphere_points(1.0, h)
+        errs.append(np.abs(oracle.stokes_dl(p, 3 * h, p["nrm"]) - p["nrm"]).max())
+    assert errs[1] < 1e-4 and errs[0] / errs[1] > 30
+
+
+def test_local_solves_fig4_rate():
+    d8, _ = _darcy_fig4(1 / 8)
+    d16, it16 = _darcy_fig4(1 / 16)
+    s8, _ = _stokes_fig4(1 / 8)
+    s16, its16 = _stokes_fig4(1 / 16)
+    assert d16 < 2e-4 and s16 < 1e-4
+    # Fig. 4 shows O(h^5); require better than fourth order between these h
+    assert d8 / d16 > 16 and s8 / s16 > 16
+    assert it16 < 20 and its16 < 25
+
+
+def test_local_sa_matches_gmres():
+    # Stokes problem of the benchmark: exact Joseph-Tao traction, U = e_z.
+    # Table 1 reports 26 local SA sweeps for Stokes and 37 for Darcy at the
+    # first D-N steps.
+    h, kappa = 1 / 8, 1.0
+    p = Q.sphere_points(1.0, h)
+    pe = A.jt_pressure_darcy(p["xyz"], 1.0, kappa, 1.0, [0, 0, 1.0])
+    f = S.traction_joseph_tao(p, pe, 1.0, kappa, 1.0, [0, 0, 1.0])
+    ug, _, _ = S.stokes_solve(p, 3 * h, 1.0, f, [0, 0, 1.0], tol=1e-11)
+    us, its, _ = S.stokes_solve(p, 3 * h, 1.0, f, [0, 0, 1.0], tol=1e-11, use_sa=True)
+    assert np.abs(ug - us).max() < 1e-8 and 10 < its < 200
+    q = (ug * p["nrm"]).sum(0)
+    pg, _, _ = S.darcy_solve(p, 3 * h, 1.0, kappa, q, tol=1e-11)
+    ps, itd, _ = S.darcy_solve(p, 3 * h, 1.0, kappa, q, tol=1e-11, use_sa=True)
+    assert np.abs(pg - ps).max() < 1e-8 and 10 < itd < 200
+
+
+@pytest.fixture(scope="module")
+def sph8():
+    return Q.sphere_points(1.0, 1 / 8)
+
+
+def test_ddm_sa_contraction_matches_n1_multiplier(sph8):
+    # benchmark-mode n = 1 multiplier A = (1 - theta) - theta R^2 / (3 kappa):
+    # 1/3 for theta = 0.5, kappa = 1; Table 1 prints 19 D-N SA iterations
+    r = S.ddm_solve(sph8, 3 / 8, 1.0, 1.0, 0.0, [0, 0, 1.0], 0.5, tol=1e-9, maxit=60,
+                    outer="sa", traction="jt")
+    hist = r["hist"]
+    ratios = [hist[k + 1] / hist[k] for k in range(4, len(hist) - 1)]
+    assert np.allclose(ratios, 1 / 3, rtol=0.03)
+    assert 19 <= r["outer_its"] <= 21
+    r75 = S.ddm_solve(sph8, 3 / 8, 1.0, 1.0, 0.0, [0, 0, 1.0], 0.75, tol=1e-9, maxit=60,
+                      outer="sa", traction="jt")
+    assert r75["outer_its"] <= r["outer_its"] // 2
+    assert np.allclose(r75["q"], r["q"], atol=1e-8)
+
+
+def test_ddm_gmres_matches_sa_and_drag(sph8):
+    ra = S.ddm_solve(sph8, 3 / 8, 1.0, 1.0, 0.0, [0, 0, 1.0], 0.75, tol=1e-10, maxit=60,
+                     outer="sa", traction="jt")
+    rg = S.ddm_solve(sph8, 3 / 8, 1.0, 1.0, 0.0, [0, 0, 1.0], 0.75, tol=1e-10, maxit=60,
+                     outer="gmres", traction="jt")
+    assert np.abs(ra["p"] - rg["p"]).max() < 1e-8
+    assert np.abs(ra["u"] - rg["u"]).max() < 1e-8
+    assert rg["outer_its"] <= 6
+    D = A.jt_drag(1.0, 1.0, 1.0, 1.0)
+    assert abs(rg["drag"][2] - D) / D < 1e-2
+    assert abs(rg["drag"][0]) < 1e-10 and abs(rg["drag"][1]) < 1e-10
+
+
+@pytest.mark.parametrize("row", [r for r in read_golden("porous_sphere_errors.txt") if r[1] == "16"][:2],
+                         ids=lambda r: "kappa%s-h1/%s" % (r[0], r[1]))
+def test_ddm_reproduces_printed_errors(row):
+    kappa, inv_h, N, itD, itS, perr, uerr, _ = row
+    kappa, h = float(kappa), 1.0 / int(inv_h)
+    p = Q.sphere_points(1.0, h)
+    assert p["w"].size == int(N)
+    r = S.ddm_solve(p, 3 * h, 1.0, kappa, 0.0, [0, 0, 1.0], 0.75 * min(kappa, 1.0), tol=1e-9,
+                    maxit=50, outer="gmres", traction="jt")
+    pe = A.jt_pressure_darcy(p["xyz"], 1.0, kappa, 1.0, [0, 0, 1.0])
+    ue = A.jt_velocity_stokes(p["xyz"], 1.0, kappa, 1.0, [0, 0, 1.0])
+    # the printed values have four significant digits
+    assert S.rms(r["p"] - pe) == pytest.approx(float(perr), rel=2e-3)
+    assert S.rms(r["u"] - ue) == pytest.approx(float(uerr), rel=2e-3)
+    if kappa == 1.0:
+        # local GMRES counts per D-N step printed beside the errors
+        assert r["inner_its"][-1] == (int(itD), int(itS))
+
+
+def test_ddm_bjs_mode_fixed_point(sph8):
+    # BJS traction (gamma != 0): no printed values exist; check that the
+    # returned state is a fixed point of the sweep and that the outer
+    # GMRES and SA agree where SA converges (kappa = 1).
+    kw = dict(mu=1.0, kappa=1.0, gamma=0.5, uinf=[0.0, 0.0, 1.0], theta=0.5, tol=1e-10, maxit=80)
+    rg = S.ddm_solve(sph8, 3 / 8, outer="gmres", traction="bjs", **kw)
+    rs = S.ddm_solve(sph8, 3 / 8, outer="sa", traction="bjs", **kw)
+    assert np.abs(rg["u"] - rs["u"]).max() < 1e-7
+    n = sph8["nrm"]
+    assert np.abs(rg["q"] - (rg["u"] * n).sum(0)).max() < 1e-8
+    f = S.traction_bjs(sph8, rg["p"], rg["u"], 1.0, 0.5)
+    assert np.abs(f - rg["f"]).max() < 1e-7
