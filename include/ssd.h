@@ -1,0 +1,273 @@
+/*
+ * ssd.h -- C ABI of libssd: regularized boundary integrals for the coupled
+ * Stokes-Darcy problem solved by Dirichlet-Neumann domain decomposition
+ * (Tlupova, "A domain decomposition solution of the Stokes-Darcy system in
+ * 3D based on boundary integrals", arXiv 2110.10749).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an int status (enum ssd_status).  On failure the
+ *   context keeps a one-line message, read with ssd_ctx_last_error().
+ * - n is the outward unit normal of the porous body, i.e. it points into the
+ *   fluid (the paper's n_D on the interface; n_S = -n).  yhat = y - x for a
+ *   target y and a source x, r = |yhat|, rho = r / delta.
+ * - Point sets and densities are structure-of-arrays in FP64:
+ *   xyz[3][n] = x row, y row, z row; a vector density u[3][n] likewise.
+ * - Buffers passed to ssd_* calls are DEVICE pointers owned by the caller,
+ *   unless a parameter is marked "host".  The library owns the context, its
+ *   workspace and the prepared layouts; it never frees caller memory.
+ * - Operator calls (ssd_laplace_*, ssd_stokes_* without _solve) are
+ *   asynchronous on the given stream.  Quadrature, solver and layout calls
+ *   synchronise the stream before they return, because they report counts
+ *   or iteration results to the host.
+ * - prec selects the arithmetic of the pair sums: SSD_FP64 (plain double) or
+ *   SSD_FP32C (single precision pair terms, compensated two-float
+ *   accumulation per target, FP64 epilogue).  Krylov and interface
+ *   arithmetic is always FP64.
+ * - Non-finite scalar arguments, n <= 0, delta <= 0, mu <= 0, kappa <= 0,
+ *   theta outside (0,1] and NULL required pointers give SSD_EINVAL before any
+ *   work is enqueued.
+ * - A context is used by one host thread at a time.
+ */
+#ifndef SSD_H
+#define SSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssd_ctx ssd_ctx;
+typedef struct ssd_layout ssd_layout;
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *ssd_stream;
+
+enum ssd_status {
+    SSD_OK = 0,
+    SSD_EINVAL = 1,    /* invalid argument */
+    SSD_ENOMEM = 2,    /* device or pinned allocation failed */
+    SSD_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    SSD_ENOTCONV = 4,  /* iteration limit reached; outputs hold the last iterate */
+    SSD_ENUMERIC = 5   /* NaN or Inf appeared in a residual */
+};
+
+enum ssd_precision { SSD_FP64 = 0, SSD_FP32C = 1 };
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (which becomes current for the
+ * calling thread).  *ctx receives the handle. */
+int ssd_ctx_create(ssd_ctx **ctx, int device);
+/* Free the context, its workspace and layouts.  NULL is accepted. */
+int ssd_ctx_destroy(ssd_ctx *ctx);
+/* Static text of a status code. */
+const char *ssd_status_string(int status);
+/* Message of the last failure on this context ("" if none). */
+const char *ssd_ctx_last_error(const ssd_ctx *ctx);
+
+/* Kernel timing.  When enabled, the library brackets every pair-sum launch
+ * with CUDA events on the launching stream.  Statistics per kernel class
+ * (enum ssd_kernel_class) accumulate until reset; reading them synchronises
+ * the recorded events.  pairs counts ordered (target, source) pairs. */
+enum ssd_kernel_class {
+    SSD_K_LAPLACE_SL = 0, SSD_K_LAPLACE_DL = 1, SSD_K_STOKES_SL = 2,
+    SSD_K_STOKES_DL = 3, SSD_K_STOKES_SLDL = 4, SSD_K_LAPLACE_SLDL = 5,
+    SSD_K_COUNT = 6
+};
+typedef struct {
+    int64_t launches;  /* pair-sum kernel launches */
+    double ms;         /* summed device time of those launches */
+    double pairs;      /* ordered pairs evaluated */
+} ssd_kernel_stats;
+int ssd_ctx_set_timing(ssd_ctx *ctx, int enable);
+int ssd_ctx_kernel_stats(ssd_ctx *ctx, int kernel_class, int precision, ssd_kernel_stats *out /* host */);
+int ssd_ctx_reset_stats(ssd_ctx *ctx);
+/* Total kernel launches the library issued since the context was created
+ * (every kernel of the library, not only the pair sums). */
+int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out /* host */);
+
+/* ------------------------------------------------------------- quadrature */
+
+/* Surfaces of Section 5.4 (eqs. Sphere, Ellipsoid): level sets phi = 0 with
+ * phi > 0 outside.  SPHERE uses abc[0] as the radius. */
+enum ssd_surface_kind { SSD_SPHERE = 0, SSD_ELLIPSOID = 1 };
+typedef struct {
+    int kind;
+    double center[3];
+    double abc[3];     /* semi-axes (ELLIPSOID); abc[0] = R (SPHERE) */
+} ssd_surface;
+
+/*
+ * Quadrature points of Section 5.4 (eq. Quadrature).  For each axis e_i the
+ * grid lines of spacing h anchored at the origin, through (j1 h, j2 h) in the
+ * other two coordinates, are intersected with the surface; an intersection x
+ * is kept when |n(x) . e_i| >= cos(angle_deg) and gets the weight
+ * psi_i(n) h^2 / |n_i|, with psi_i = b(acos|n_i|/theta) / sum_j b(acos|n_j|/theta),
+ * b(r) = exp(r^2/(r^2-1)) for |r| < 1 (theta = angle_deg in radians).
+ * Order: axis 0,1,2; j1 ascending; j2 ascending; smaller root first.
+ * meta[4][n] = (axis, j1, j2, branch) with branch 0 for the smaller root.
+ * Pass xyz == NULL to query the count only (*n_out).  Otherwise capacity
+ * must be >= the count (else SSD_EINVAL with *n_out set to the count).
+ * Points and normals are computed with correctly rounded +,-,*,/,sqrt only.
+ * Synchronises `stream`.
+ */
+int ssd_quadrature_points(ssd_ctx *ctx, const ssd_surface *surf /* host */, double h,
+                          double angle_deg, int64_t capacity, int64_t *n_out /* host */,
+                          double *xyz, double *nrm, double *w, int32_t *meta,
+                          ssd_stream stream);
+
+/* ----------------------------------------------------------------- points */
+
+typedef struct {
+    int64_t n;
+    const double *xyz;   /* [3][n] device */
+    const double *nrm;   /* [3][n] device, unit outward normals */
+    const double *w;     /* [n] device, quadrature weights */
+    ssd_layout *layout;  /* optional: from ssd_points_prepare(); NULL = per-call packing */
+} ssd_points;
+
+/* Build a device layout of the point set for the pair kernels: FP32 copies
+ * of positions, weighted normals and weights in a spatially sorted order,
+ * and per-tile bounding boxes for the near/far split.  Stores the handle in
+ * pts->layout.  The layout refers to the point data by value: it must be
+ * rebuilt if the points change.  Synchronises `stream`. */
+int ssd_points_prepare(ssd_ctx *ctx, ssd_points *pts /* host struct */, ssd_stream stream);
+/* Release a layout built by ssd_points_prepare and clear pts->layout. */
+int ssd_points_release(ssd_ctx *ctx, ssd_points *pts /* host struct */);
+
+/* ---------------------------------------------------------- layer operators
+ * All four follow Sections 5.1-5.3 with the smoothed kernels of Section 5.3:
+ *   s1 = erf(rho) - 2/(3 sqrt(pi)) rho (2 rho^2 - 5) e^{-rho^2}
+ *   s2 = erf(rho) + 2/(3 sqrt(pi)) rho (2 rho^2 - 3) e^{-rho^2}
+ *   s3 = erf(rho) - 2/(3 sqrt(pi)) rho (4 rho^4 - 14 rho^2 + 3) e^{-rho^2}
+ *   s4 = erf(rho) - 2/(9 sqrt(pi)) rho (8 rho^6 - 36 rho^4 + 6 rho^2 + 9) e^{-rho^2}
+ * summed over every quadrature point x_j (weight w_j) for every target
+ * y_i = x_i, the self pair included at its finite limit.
+ */
+
+/* (L g)(y) = sum_x w g G^delta,  G^delta = -s1(rho) / (4 pi r)  (Section 5.1, 5.3). */
+int ssd_laplace_SL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *g,
+                   double *out, int prec, ssd_stream stream);
+/* (D^L p)(y) = sum_x w [p(x) - p(y)] dG^delta/dn_x,
+ * dG^delta/dn_x = -(yhat . n_x) s2(rho) / (4 pi r^3).  D^L = H - I/2 (eq. H_subtr). */
+int ssd_laplace_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *p,
+                   double *out, int prec, ssd_stream stream);
+/* (M f)(y) = 1/(8 pi mu) sum_x w S^delta f,
+ * S^delta_ab = delta_ab s1/r + yhat_a yhat_b s3/r^3  (Section 5.2, 5.3).  f, out [3][n]. */
+int ssd_stokes_SL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu,
+                  const double *f, double *out, int prec, ssd_stream stream);
+/* (D^S u)(y) = -1/(8 pi) sum_x w [u(x) - u(y)]_a T^delta_abc n_c(x),
+ * T^delta_abc = -6 yhat_a yhat_b yhat_c s4/r^5.  D^S = K + I/2 (eq. K_subtr).  u, out [3][n]. */
+int ssd_stokes_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u,
+                  double *out, int prec, ssd_stream stream);
+/* One pass sharing r, erf and exp between both layers:
+ * out = alpha (M f) + beta (D^S u)   [Stokes],   out = alpha (L g) + beta (D^L p)   [Laplace].
+ * Used for the right-hand sides and residuals b - A x of the local solves. */
+int ssd_stokes_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu,
+                    const double *f, const double *u, double alpha, double beta,
+                    double *out, int prec, ssd_stream stream);
+int ssd_laplace_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *g,
+                     const double *p, double alpha, double beta, double *out, int prec,
+                     ssd_stream stream);
+
+/* ------------------------------------------------------------ local solves */
+
+typedef struct {
+    double tol;    /* stop when ||b - A x|| <= tol ||b|| (GMRES estimate) or, for SA,
+                      when ||x_k - x_{k-1}|| <= tol ||x_k|| */
+    int maxit;     /* total iteration limit */
+    int restart;   /* GMRES restart length m (1..128) */
+    int use_sa;    /* 1: successive approximations (eqs. Darcy_BIEM_iter,
+                      Stokes_BIEM_iter) instead of GMRES */
+    int prec;      /* enum ssd_precision of the pair sums */
+    int deflate;   /* Stokes solves: 1 adds n (w . (u.n))/sum(w) to the operator.  The
+                      continuous I/2 - K has the normal field in its null space, so
+                      I - D^S has a near-null vector (eigenvalue O(h^5)) that amplifies
+                      rounding, most of all in FP32C; the rank-one term removes it and
+                      selects the zero-net-flux solution (int u.n dS = 0, the Darcy
+                      compatibility condition).  0 = the operator as printed. */
+} ssd_krylov;
+
+/*
+ * Darcy pressure on the interface (eq. Darcy_final): 1/2 p = H p + b_D with
+ * b_D = (mu/kappa) L q, q = u_D . n the normal Darcy velocity.  Solved as
+ * -D^L p + (w . p)/sum(w) = b_D: the operator annihilates constants and the
+ * rank-one term fixes the gauge without changing the solution of a
+ * consistent system.  p_out has zero quadrature-weighted mean.
+ * iters, relres: host.  Synchronises `stream`.
+ */
+int ssd_darcy_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu,
+                    double kappa, const double *q, double *p_out, const ssd_krylov *kr,
+                    int *iters, double *relres, ssd_stream stream);
+/*
+ * Stokes velocity on the interface (eq. Stokes_final): 1/2 u = K u + b_S with
+ * b_S = U_inf - M f, solved as (I - D^S) u = b_S.  f, u_out [3][n];
+ * uinf, iters, relres: host.  Synchronises `stream`.
+ */
+int ssd_stokes_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu,
+                     const double *f, const double uinf[3], double *u_out,
+                     const ssd_krylov *kr, int *iters, double *relres, ssd_stream stream);
+
+/* ------------------------------------------------- Dirichlet-Neumann solve */
+
+enum ssd_traction_mode {
+    SSD_TRACTION_BJS = 0,         /* f = -p_D n + s (gamma/sqrt(kappa)) (u - (u.n) n), eq. f */
+    SSD_TRACTION_JOSEPH_TAO = 1   /* porous-sphere benchmark of Section 7.3 (eqs. f_r, f_theta) */
+};
+
+typedef struct {
+    double mu, kappa, gamma;   /* viscosity, permeability, BJS coefficient */
+    double uinf[3];            /* far-field velocity */
+    double delta;              /* smoothing radius (the paper uses 3h) */
+    double theta;              /* relaxation (eq. q_update), in (0,1] */
+    double tol_outer;          /* DDM residual (SA) or interface GMRES tolerance */
+    int maxit_outer;
+    int outer_gmres;           /* 0: relaxed sweeps (SA); 1: GMRES on the interface */
+    int traction_mode;         /* enum ssd_traction_mode */
+    int bjs_implicit;          /* BJS mode: 0 = slip term from the previous sweep's
+                                  velocity (Section 3, step 2, as printed); 1 = slip
+                                  term at the Stokes step's own velocity, i.e.
+                                  (I - D^S) u + s (gamma/sqrt(kappa)) M(u - (u.n) n)
+                                  = U_inf + M(p_D n), one fused SL+DL pass per
+                                  matvec; the interface state is then q alone */
+    double bjs_sign;           /* s in the BJS traction: +1 (default) or -1 */
+    double radius;             /* sphere radius R (JOSEPH_TAO mode; sphere centred at 0) */
+    ssd_krylov inner;          /* local solves; inner.tol applies to both */
+} ssd_ddm_params;
+
+/*
+ * Dirichlet-Neumann iteration of Sections 3 and 6.  From q = 0, u_prev = 0,
+ * each sweep: b_D = (mu/kappa) L q; Darcy solve for p_D; traction f from p_D
+ * (and u_prev in BJS mode); b_S = U_inf - M f; Stokes solve for u_S;
+ * q <- (1 - theta) q + theta u_S . n.
+ * outer_gmres = 0: sweeps until ||q_k - q_{k-1}|| <= tol ||q_k|| (eq. DDM_residual).
+ * outer_gmres = 1: GMRES on the affine interface map z -> G z + c,
+ *   z = q (JOSEPH_TAO mode, gamma = 0, or bjs_implicit) or z = (q, u_prev) (lagged BJS),
+ *   then one sweep from the solution gives the returned fields.
+ * Outputs (device): q[n], p_D[n], u_S[3][n], f_S[3][n] (any may be NULL).
+ * Host outputs: drag[3] = sum_x w f (eq. drag_int), *outer_its,
+ *   inner_its[2 * max(maxit_outer + 2, 1)] = (Darcy, Stokes) iterations per sweep,
+ *   res_hist[maxit_outer] = DDM residual per sweep (SA) or the final
+ *   interface residual (GMRES, res_hist[0]).  Host pointers may be NULL.
+ * Synchronises `stream`.
+ */
+int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
+                  double *q, double *p_D, double *u_S, double *f_S, double drag[3],
+                  int *outer_its, int *inner_its, double *res_hist, ssd_stream stream);
+
+/*
+ * Same solve with HOST buffers: copies xyz[3][n], nrm[3][n], w[n] to the
+ * device, prepares the layout, solves, and copies q, p_D, u_S, f_S back
+ * (host outputs may be NULL).  Pinned host memory gives the fastest copies.
+ */
+int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double *nrm,
+                       const double *w, const ssd_ddm_params *prm, double *q, double *p_D,
+                       double *u_S, double *f_S, double drag[3], int *outer_its,
+                       int *inner_its, double *res_hist, ssd_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSD_H */

@@ -64,9 +64,9 @@ def lib():
             L.ssdo_s.argtypes = [i32, d]
             L.ssdo_s.restype = d
             L.ssdo_laplace_sl.argtypes = [i64, P, i64, P, P, d, P, P]
-            L.ssdo_laplace_dl.argtypes = [i64, P, P, P, d, P, P]
+            L.ssdo_laplace_dl.argtypes = [i64, P, P, P, d, P, i64, P, P]
             L.ssdo_stokes_sl.argtypes = [i64, P, i64, P, P, d, d, P, P]
-            L.ssdo_stokes_dl.argtypes = [i64, P, P, P, d, P, P]
+            L.ssdo_stokes_dl.argtypes = [i64, P, P, P, d, P, i64, P, P]
             L.ssdo_num_threads.restype = i32
             _lib = L
     return _lib
@@ -111,13 +111,24 @@ def laplace_sl(pts, delta, g, targets=None):
     return out
 
 
-def laplace_dl(pts, delta, p):
-    """(D^L p)(y) = sum_x w [p(x) - p(y)] dG^delta/dn_x  (eq. H_subtr)."""
+def _rows(rows):
+    if rows is None:
+        return None, 0, None
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    return r, r.size, r.ctypes.data_as(ctypes.c_void_p)
+
+
+def laplace_dl(pts, delta, p, rows=None):
+    """(D^L p)(y) = sum_x w [p(x) - p(y)] dG^delta/dn_x  (eq. H_subtr).
+
+    rows: optional target indices; the result then holds those targets only.
+    """
     xyz, n_, w = _c(pts["xyz"]), _c(pts["nrm"]), _c(pts["w"])
     p = _c(p)
     n = xyz[0].shape[1]
-    out = np.empty(n)
-    lib().ssdo_laplace_dl(n, xyz[1], n_[1], w[1], float(delta), p[1],
+    keep, nr, pr = _rows(rows)
+    out = np.empty(nr if rows is not None else n)
+    lib().ssdo_laplace_dl(n, xyz[1], n_[1], w[1], float(delta), p[1], nr, pr,
                           out.ctypes.data_as(ctypes.c_void_p))
     return out
 
@@ -137,12 +148,16 @@ def stokes_sl(pts, delta, mu, f, targets=None):
     return out
 
 
-def stokes_dl(pts, delta, u):
-    """(D^S u)(y) = -1/(8 pi) sum_x w [u(x)-u(y)].T^delta.n_x  (eq. K_subtr)."""
+def stokes_dl(pts, delta, u, rows=None):
+    """(D^S u)(y) = -1/(8 pi) sum_x w [u(x)-u(y)].T^delta.n_x  (eq. K_subtr).
+
+    rows: optional target indices; the result is then [3][len(rows)].
+    """
     xyz, n_, w = _c(pts["xyz"]), _c(pts["nrm"]), _c(pts["w"])
     u = _c(u)
     n = xyz[0].shape[1]
-    out = np.empty((3, n))
-    lib().ssdo_stokes_dl(n, xyz[1], n_[1], w[1], float(delta), u[1],
+    keep, nr, pr = _rows(rows)
+    out = np.empty((3, nr if rows is not None else n))
+    lib().ssdo_stokes_dl(n, xyz[1], n_[1], w[1], float(delta), u[1], nr, pr,
                          out.ctypes.data_as(ctypes.c_void_p))
     return out

@@ -126,10 +126,14 @@ void ssdo_laplace_sl(int64_t nt, const double *ty, int64_t ns, const double *sx,
  * Targets coincide with sources (p_i is the density at target i).
  */
 void ssdo_laplace_dl(int64_t n, const double *xyz, const double *nrm, const double *w,
-                     double delta, const double *p, double *out) {
+                     double delta, const double *p, int64_t nrows, const int64_t *rows,
+                     double *out) {
+    /* rows == NULL: every target; otherwise out[k] is the value at target rows[k] */
     double d3 = delta * delta * delta;
+    int64_t nt = rows ? nrows : n;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = 0; k < nt; ++k) {
+        int64_t i = rows ? rows[k] : k;
         double y0 = xyz[i], y1 = xyz[n + i], y2 = xyz[2 * n + i];
         double acc = 0.0;
         for (int64_t j = 0; j < n; ++j) {
@@ -139,7 +143,7 @@ void ssdo_laplace_dl(int64_t n, const double *xyz, const double *nrm, const doub
             double K = -yn * ssdo_sigma(2, r / delta) / (4.0 * PI_D * d3);
             acc += w[j] * (p[j] - p[i]) * K;
         }
-        out[i] = acc;
+        out[k] = acc;
     }
 }
 
@@ -186,10 +190,14 @@ void ssdo_stokes_sl(int64_t nt, const double *ty, int64_t ns, const double *sx,
  * n is the outward normal of the porous body (into the fluid).
  */
 void ssdo_stokes_dl(int64_t n, const double *xyz, const double *nrm, const double *w,
-                    double delta, const double *u, double *out) {
+                    double delta, const double *u, int64_t nrows, const int64_t *rows,
+                    double *out) {
+    /* rows == NULL: every target; otherwise column k of out ([3][nrows]) is target rows[k] */
     double d5 = delta * delta * delta * delta * delta;
+    int64_t nt = rows ? nrows : n;
 #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = 0; k < nt; ++k) {
+        int64_t i = rows ? rows[k] : k;
         double y0 = xyz[i], y1 = xyz[n + i], y2 = xyz[2 * n + i];
         double ui0 = u[i], ui1 = u[n + i], ui2 = u[2 * n + i];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -206,9 +214,9 @@ void ssdo_stokes_dl(int64_t n, const double *xyz, const double *nrm, const doubl
             a1 += c * d1;
             a2 += c * d2;
         }
-        out[i] = a0;
-        out[n + i] = a1;
-        out[2 * n + i] = a2;
+        out[k] = a0;
+        out[nt + k] = a1;
+        out[2 * nt + k] = a2;
     }
 }
 

@@ -135,14 +135,49 @@ def darcy_solve(pts, delta, mu, kappa, q, tol=1e-9, restart=50, maxit=1000, use_
     return p - weighted_mean(pts, p), its, rel
 
 
-def stokes_solve(pts, delta, mu, f, uinf, tol=1e-9, restart=50, maxit=1000, use_sa=False):
-    """Solve (I - D^S) u = U_inf - M f for the interface velocity [3][N]."""
+def normal_flux_term(pts, u):
+    """n (w . (u . n)) / sum(w): rank-one term on the normal mode."""
+    n = pts["nrm"]
+    return n * (float(pts["w"] @ (u * n).sum(0)) / float(pts["w"].sum()))
+
+
+def stokes_solve(pts, delta, mu, f, uinf, tol=1e-9, restart=50, maxit=1000, use_sa=False, deflate=False):
+    """Solve (I - D^S) u = U_inf - M f for the interface velocity [3][N].
+
+    deflate: the continuous I/2 - K has the normal field n in its null space,
+    so the discrete I - D^S has a near-null vector (eigenvalue O(h^5)).  With
+    deflate, GMRES runs on (I - D^S) u + n (w . (u.n))/sum(w): nonsingular,
+    and its solution is the one with zero net flux  int u.n dS = 0 (the
+    Darcy compatibility condition on q = u.n).
+    """
     b = np.asarray(uinf, dtype=np.float64)[:, None] - oracle.stokes_sl(pts, delta, mu, f)
     if use_sa:
         # eq. Stokes_BIEM_iter: u <- u/2 + K u + b = D^S u + b
         return successive_approx(lambda u: oracle.stokes_dl(pts, delta, u) + b,
                                  np.zeros_like(b), tol, maxit)
+    if deflate:
+        return gmres(lambda u: u - oracle.stokes_dl(pts, delta, u) + normal_flux_term(pts, u), b, tol,
+                     restart, maxit)
     return gmres(lambda u: u - oracle.stokes_dl(pts, delta, u), b, tol, restart, maxit)
+
+
+def stokes_solve_bjs_implicit(pts, delta, mu, p, uinf, kappa, gamma, sign=1.0, tol=1e-9, restart=50,
+                              maxit=1000, deflate=False):
+    """Stokes solve with the BJS slip term taken at the current velocity.
+
+    With f = -p n + s c P u (c = gamma/sqrt(kappa), P u = u - (u.n) n),
+    u = D^S u + U_inf - M f becomes
+        (I - D^S) u + s c M(P u) = U_inf + M(p n).
+    """
+    n = pts["nrm"]
+    c = sign * gamma / math.sqrt(kappa)
+    b = np.asarray(uinf, dtype=np.float64)[:, None] + oracle.stokes_sl(pts, delta, mu, p * n)
+
+    def A(u):
+        Pu = u - (u * n).sum(0) * n
+        v = u - oracle.stokes_dl(pts, delta, u) + c * oracle.stokes_sl(pts, delta, mu, Pu)
+        return v + normal_flux_term(pts, u) if deflate else v
+    return gmres(A, b, tol, restart, maxit)
 
 
 def traction_bjs(pts, p, u_prev, kappa, gamma, sign=1.0):
@@ -164,7 +199,8 @@ def traction_joseph_tao(pts, p, R, kappa, mu, uinf):
 
 def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
               outer="sa", traction="bjs", R=1.0, bjs_sign=1.0,
-              inner_tol=None, restart=50, inner_maxit=1000, use_sa=False):
+              inner_tol=None, restart=50, inner_maxit=1000, use_sa=False, bjs_implicit=False,
+              deflate=False):
     """Dirichlet-Neumann iteration of Sections 3 and 6.
 
     One sweep G maps (q, u_prev) to (q_new, u): Darcy solve with Neumann data
@@ -176,6 +212,10 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
     (q, u_prev) in BJS mode with gamma != 0); GMRES solves (I - G) z = c with
     relative residual tol, and one final sweep from the solution gives the
     returned fields.
+    bjs_implicit: the Stokes step imposes the BJS slip at its own velocity
+    (see stokes_solve_bjs_implicit) instead of the previous sweep's, so the
+    interface state is q alone.
+    deflate: Stokes solves remove the near-null normal mode (see stokes_solve).
     Returns a dict with q, p, u, f, drag, outer iteration count, inner counts
     and the residual history.
     """
@@ -184,16 +224,22 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
     uinf = np.asarray(uinf, dtype=np.float64)
     if inner_tol is None:
         inner_tol = tol if outer == "sa" else 0.1 * tol
-    stacked = (traction == "bjs" and gamma != 0.0)
+    stacked = (traction == "bjs" and gamma != 0.0 and not bjs_implicit)
     inner_its = []
 
     def sweep(q, u_prev):
         p, itd, _ = darcy_solve(pts, delta, mu, kappa, q, inner_tol, restart, inner_maxit, use_sa)
-        if traction == "bjs":
-            f = traction_bjs(pts, p, u_prev, kappa, gamma, bjs_sign)
+        if traction == "bjs" and bjs_implicit:
+            u, its, _ = stokes_solve_bjs_implicit(pts, delta, mu, p, uinf, kappa, gamma, bjs_sign,
+                                                  inner_tol, restart, inner_maxit, deflate)
+            f = traction_bjs(pts, p, u, kappa, gamma, bjs_sign)
         else:
-            f = traction_joseph_tao(pts, p, R, kappa, mu, uinf)
-        u, its, _ = stokes_solve(pts, delta, mu, f, uinf, inner_tol, restart, inner_maxit, use_sa)
+            if traction == "bjs":
+                f = traction_bjs(pts, p, u_prev, kappa, gamma, bjs_sign)
+            else:
+                f = traction_joseph_tao(pts, p, R, kappa, mu, uinf)
+            u, its, _ = stokes_solve(pts, delta, mu, f, uinf, inner_tol, restart, inner_maxit, use_sa,
+                                     deflate)
         inner_its.append((itd, its))
         qn = (1.0 - theta) * q + theta * (u * n).sum(0)
         return qn, u, p, f

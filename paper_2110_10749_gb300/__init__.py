@@ -1,0 +1,380 @@
+"""Python binding of libssd (C ABI in include/ssd.h).
+
+Regularized boundary integrals and the Dirichlet-Neumann solve of the
+coupled Stokes-Darcy problem (arXiv 2110.10749) on sm_103a.  This module only
+marshals arguments: every step of the computation runs in the CUDA library.
+PyTorch supplies device memory and the current stream.  Importing works
+without a GPU; every call that computes needs the built library and a GPU and
+raises if either is missing (there is no CPU fallback).
+
+Functions keep the C names without the ``ssd_`` prefix.  Arrays are
+structure-of-arrays float64 CUDA tensors: points and vector densities have
+shape (3, n), scalars (n,).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libssd.so")
+
+SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECUDA, SSD_ENOTCONV, SSD_ENUMERIC = range(6)
+FP64, FP32C = 0, 1
+SPHERE, ELLIPSOID = 0, 1
+TRACTION_BJS, TRACTION_JOSEPH_TAO = 0, 1
+K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_SLDL = range(6)
+
+# Every entry point declared in include/ssd.h.
+EXPORTS = [
+    "ssd_ctx_create", "ssd_ctx_destroy", "ssd_status_string", "ssd_ctx_last_error",
+    "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count",
+    "ssd_quadrature_points", "ssd_points_prepare", "ssd_points_release",
+    "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
+    "ssd_stokes_SLDL", "ssd_laplace_SLDL",
+    "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
+]
+
+
+class SsdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class NotConverged(SsdError):
+    pass
+
+
+class Layout(C.Structure):
+    pass
+
+
+class CPoints(C.Structure):
+    _fields_ = [("n", C.c_int64), ("xyz", C.c_void_p), ("nrm", C.c_void_p), ("w", C.c_void_p),
+                ("layout", C.POINTER(Layout))]
+
+
+class CSurface(C.Structure):
+    _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("abc", C.c_double * 3)]
+
+
+class CKrylov(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("use_sa", C.c_int),
+                ("prec", C.c_int), ("deflate", C.c_int)]
+
+
+class CDdmParams(C.Structure):
+    _fields_ = [("mu", C.c_double), ("kappa", C.c_double), ("gamma", C.c_double), ("uinf", C.c_double * 3),
+                ("delta", C.c_double), ("theta", C.c_double), ("tol_outer", C.c_double),
+                ("maxit_outer", C.c_int), ("outer_gmres", C.c_int), ("traction_mode", C.c_int),
+                ("bjs_implicit", C.c_int), ("bjs_sign", C.c_double), ("radius", C.c_double), ("inner", CKrylov)]
+
+
+class CKernelStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("pairs", C.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib():
+    """Load libssd.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libssd.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2110_10749_gb300.build): %s" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P, i, d, i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    sig = {
+        "ssd_ctx_create": [C.POINTER(P), i],
+        "ssd_ctx_destroy": [P],
+        "ssd_status_string": [i],
+        "ssd_ctx_last_error": [P],
+        "ssd_ctx_set_timing": [P, i],
+        "ssd_ctx_kernel_stats": [P, i, i, C.POINTER(CKernelStats)],
+        "ssd_ctx_reset_stats": [P],
+        "ssd_ctx_launch_count": [P, C.POINTER(i64)],
+        "ssd_quadrature_points": [P, C.POINTER(CSurface), d, d, i64, C.POINTER(i64), P, P, P, P, P],
+        "ssd_points_prepare": [P, C.POINTER(CPoints), P],
+        "ssd_points_release": [P, C.POINTER(CPoints)],
+        "ssd_laplace_SL": [P, C.POINTER(CPoints), d, P, P, i, P],
+        "ssd_laplace_DL": [P, C.POINTER(CPoints), d, P, P, i, P],
+        "ssd_stokes_SL": [P, C.POINTER(CPoints), d, d, P, P, i, P],
+        "ssd_stokes_DL": [P, C.POINTER(CPoints), d, P, P, i, P],
+        "ssd_stokes_SLDL": [P, C.POINTER(CPoints), d, d, P, P, d, d, P, i, P],
+        "ssd_laplace_SLDL": [P, C.POINTER(CPoints), d, P, P, d, d, P, i, P],
+        "ssd_darcy_solve": [P, C.POINTER(CPoints), d, d, d, P, P, C.POINTER(CKrylov), C.POINTER(i),
+                            C.POINTER(d), P],
+        "ssd_stokes_solve": [P, C.POINTER(CPoints), d, d, P, C.POINTER(d), P, C.POINTER(CKrylov),
+                             C.POINTER(i), C.POINTER(d), P],
+        "ssd_ddm_solve": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
+                          C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
+        "ssd_ddm_solve_host": [P, i64, P, P, P, C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
+                               C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.ssd_status_string.restype = C.c_char_p
+    L.ssd_ctx_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required; libssd has no CPU path")
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != _torch().float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns an ssd_ctx on one device."""
+
+    def __init__(self, device: int = 0):
+        _torch()
+        h = C.c_void_p()
+        st = lib().ssd_ctx_create(C.byref(h), int(device))
+        if st != SSD_OK:
+            raise SsdError(st, "ssd_ctx_create failed: %s" % lib().ssd_status_string(st).decode())
+        self.h = h
+        self.device = device
+
+    def check(self, st, what):
+        if st == SSD_OK:
+            return
+        msg = lib().ssd_ctx_last_error(self.h).decode()
+        cls = NotConverged if st == SSD_ENOTCONV else SsdError
+        raise cls(st, "%s: %s" % (what, msg))
+
+    def close(self):
+        if self.h:
+            lib().ssd_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_timing(self, on=True):
+        self.check(lib().ssd_ctx_set_timing(self.h, 1 if on else 0), "ssd_ctx_set_timing")
+
+    def kernel_stats(self, kernel_class, prec):
+        s = CKernelStats()
+        self.check(lib().ssd_ctx_kernel_stats(self.h, kernel_class, prec, C.byref(s)), "ssd_ctx_kernel_stats")
+        return {"launches": s.launches, "ms": s.ms, "pairs": s.pairs}
+
+    def reset_stats(self):
+        self.check(lib().ssd_ctx_reset_stats(self.h), "ssd_ctx_reset_stats")
+
+    def launch_count(self):
+        v = C.c_int64()
+        self.check(lib().ssd_ctx_launch_count(self.h, C.byref(v)), "ssd_ctx_launch_count")
+        return v.value
+
+
+class Points:
+    """A quadrature point set on the device: xyz, nrm (3, n) and w (n,)."""
+
+    def __init__(self, xyz, nrm, w):
+        torch = _torch()
+        self.xyz = xyz.to(dtype=torch.float64).contiguous()
+        self.nrm = nrm.to(dtype=torch.float64).contiguous()
+        self.w = w.to(dtype=torch.float64).contiguous()
+        self.n = int(self.w.numel())
+        assert self.xyz.shape == (3, self.n) and self.nrm.shape == (3, self.n)
+        self.c = CPoints(self.n, _ptr(self.xyz), _ptr(self.nrm), _ptr(self.w), None)
+        self.ctx = None
+
+    @classmethod
+    def from_numpy(cls, pts, device="cuda"):
+        torch = _torch()
+        return cls(torch.as_tensor(pts["xyz"], device=device), torch.as_tensor(pts["nrm"], device=device),
+                   torch.as_tensor(pts["w"], device=device))
+
+    def prepare(self, ctx):
+        ctx.check(lib().ssd_points_prepare(ctx.h, C.byref(self.c), _stream()), "ssd_points_prepare")
+        self.ctx = ctx
+        return self
+
+    def release(self):
+        if self.ctx is not None and self.c.layout:
+            lib().ssd_points_release(self.ctx.h, C.byref(self.c))
+        self.ctx = None
+
+
+def quadrature_points(ctx, kind, abc, h, angle_deg=70.0, center=(0.0, 0.0, 0.0)):
+    """Quadrature points of the sphere/ellipsoid (Section 5.4): dict of CUDA tensors."""
+    torch = _torch()
+    surf = CSurface(kind, (C.c_double * 3)(*center), (C.c_double * 3)(*(list(abc) + [0.0] * (3 - len(abc)))))
+    n = C.c_int64()
+    L = lib()
+    ctx.check(L.ssd_quadrature_points(ctx.h, C.byref(surf), float(h), float(angle_deg), 0, C.byref(n),
+                                      None, None, None, None, _stream()), "ssd_quadrature_points")
+    N = n.value
+    dev = torch.device("cuda", ctx.device)
+    xyz = torch.empty((3, N), dtype=torch.float64, device=dev)
+    nrm = torch.empty((3, N), dtype=torch.float64, device=dev)
+    w = torch.empty((N,), dtype=torch.float64, device=dev)
+    meta = torch.empty((4, N), dtype=torch.int32, device=dev)
+    ctx.check(L.ssd_quadrature_points(ctx.h, C.byref(surf), float(h), float(angle_deg), N, C.byref(n),
+                                      _ptr(xyz), _ptr(nrm), _ptr(w), C.c_void_p(meta.data_ptr()), _stream()),
+              "ssd_quadrature_points")
+    return {"xyz": xyz, "nrm": nrm, "w": w, "meta": meta}
+
+
+def _out_like(t, out):
+    return _torch().empty_like(t) if out is None else out
+
+
+def laplace_SL(ctx, pts, delta, g, prec=FP64, out=None):
+    out = _out_like(g, out)
+    ctx.check(lib().ssd_laplace_SL(ctx.h, C.byref(pts.c), float(delta), _ptr(g), _ptr(out), prec, _stream()),
+              "ssd_laplace_SL")
+    return out
+
+
+def laplace_DL(ctx, pts, delta, p, prec=FP64, out=None):
+    out = _out_like(p, out)
+    ctx.check(lib().ssd_laplace_DL(ctx.h, C.byref(pts.c), float(delta), _ptr(p), _ptr(out), prec, _stream()),
+              "ssd_laplace_DL")
+    return out
+
+
+def stokes_SL(ctx, pts, delta, mu, f, prec=FP64, out=None):
+    out = _out_like(f, out)
+    ctx.check(lib().ssd_stokes_SL(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), _ptr(out), prec,
+                                  _stream()), "ssd_stokes_SL")
+    return out
+
+
+def stokes_DL(ctx, pts, delta, u, prec=FP64, out=None):
+    out = _out_like(u, out)
+    ctx.check(lib().ssd_stokes_DL(ctx.h, C.byref(pts.c), float(delta), _ptr(u), _ptr(out), prec, _stream()),
+              "ssd_stokes_DL")
+    return out
+
+
+def stokes_SLDL(ctx, pts, delta, mu, f, u, alpha=1.0, beta=1.0, prec=FP64, out=None):
+    out = _out_like(u, out)
+    ctx.check(lib().ssd_stokes_SLDL(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), _ptr(u),
+                                    float(alpha), float(beta), _ptr(out), prec, _stream()), "ssd_stokes_SLDL")
+    return out
+
+
+def laplace_SLDL(ctx, pts, delta, g, p, alpha=1.0, beta=1.0, prec=FP64, out=None):
+    out = _out_like(p, out)
+    ctx.check(lib().ssd_laplace_SLDL(ctx.h, C.byref(pts.c), float(delta), _ptr(g), _ptr(p), float(alpha),
+                                     float(beta), _ptr(out), prec, _stream()), "ssd_laplace_SLDL")
+    return out
+
+
+def krylov(tol=1e-9, maxit=200, restart=50, use_sa=False, prec=FP64, deflate=False):
+    return CKrylov(float(tol), int(maxit), int(restart), 1 if use_sa else 0, int(prec), 1 if deflate else 0)
+
+
+def darcy_solve(ctx, pts, delta, mu, kappa, q, kr=None, out=None):
+    kr = kr or krylov()
+    out = _out_like(q, out)
+    its, rel = C.c_int(), C.c_double()
+    ctx.check(lib().ssd_darcy_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), float(kappa), _ptr(q),
+                                    _ptr(out), C.byref(kr), C.byref(its), C.byref(rel), _stream()),
+              "ssd_darcy_solve")
+    return out, its.value, rel.value
+
+
+def stokes_solve(ctx, pts, delta, mu, f, uinf, kr=None, out=None):
+    kr = kr or krylov()
+    out = _out_like(f, out)
+    its, rel = C.c_int(), C.c_double()
+    ui = (C.c_double * 3)(*uinf)
+    ctx.check(lib().ssd_stokes_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), ui, _ptr(out),
+                                     C.byref(kr), C.byref(its), C.byref(rel), _stream()), "ssd_stokes_solve")
+    return out, its.value, rel.value
+
+
+def ddm_params(mu=1.0, kappa=1.0, gamma=0.0, uinf=(0.0, 0.0, 1.0), delta=0.1, theta=0.5, tol_outer=1e-9,
+               maxit_outer=100, outer_gmres=False, traction_mode=TRACTION_BJS, bjs_sign=1.0, radius=1.0,
+               inner=None, bjs_implicit=False):
+    return CDdmParams(float(mu), float(kappa), float(gamma), (C.c_double * 3)(*uinf), float(delta), float(theta),
+                      float(tol_outer), int(maxit_outer), 1 if outer_gmres else 0, int(traction_mode),
+                      1 if bjs_implicit else 0, float(bjs_sign), float(radius), inner or krylov())
+
+
+def _ddm_out(prm, n, dev):
+    torch = _torch()
+    return {"q": torch.empty((n,), dtype=torch.float64, device=dev),
+            "p": torch.empty((n,), dtype=torch.float64, device=dev),
+            "u": torch.empty((3, n), dtype=torch.float64, device=dev),
+            "f": torch.empty((3, n), dtype=torch.float64, device=dev)}
+
+
+def ddm_solve(ctx, pts, prm, raise_on_notconv=True):
+    """Dirichlet-Neumann solve (Sections 3, 6).  Returns a dict of results."""
+    o = _ddm_out(prm, pts.n, pts.xyz.device)
+    drag = (C.c_double * 3)()
+    oits = C.c_int()
+    cap = 2 * (prm.maxit_outer + 2)
+    inner = (C.c_int * cap)()
+    hist = (C.c_double * max(prm.maxit_outer, 1))()
+    st = lib().ssd_ddm_solve(ctx.h, C.byref(pts.c), C.byref(prm), _ptr(o["q"]), _ptr(o["p"]), _ptr(o["u"]),
+                             _ptr(o["f"]), drag, C.byref(oits), inner, hist, _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_ddm_solve")
+    o["drag"] = np.array(drag[:])
+    o["outer_its"] = oits.value
+    n_sweeps = oits.value + 2 if prm.outer_gmres else oits.value
+    o["inner_its"] = [(inner[2 * k], inner[2 * k + 1]) for k in range(min(n_sweeps, cap // 2))]
+    o["hist"] = list(hist[:oits.value if not prm.outer_gmres else 1])
+    o["status"] = st
+    return o
+
+
+def ddm_solve_host(ctx, xyz, nrm, w, prm, out=None, raise_on_notconv=True):
+    """D-N solve with host (numpy or pinned CPU tensor) buffers; copies happen inside."""
+    def hp(a):
+        if hasattr(a, "data_ptr"):
+            assert not a.is_cuda and a.is_contiguous()
+            return C.c_void_p(a.data_ptr())
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a.ctypes.data_as(C.c_void_p)
+    n = int(w.shape[0])
+    out = out or {"q": np.empty(n), "p": np.empty(n), "u": np.empty((3, n)), "f": np.empty((3, n))}
+    drag = (C.c_double * 3)()
+    oits = C.c_int()
+    cap = 2 * (prm.maxit_outer + 2)
+    inner = (C.c_int * cap)()
+    hist = (C.c_double * max(prm.maxit_outer, 1))()
+    st = lib().ssd_ddm_solve_host(ctx.h, n, hp(xyz), hp(nrm), hp(w), C.byref(prm), hp(out["q"]), hp(out["p"]),
+                                  hp(out["u"]), hp(out["f"]), drag, C.byref(oits), inner, hist, _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_ddm_solve_host")
+    out["status"] = st
+    out["drag"] = np.array(drag[:])
+    out["outer_its"] = oits.value
+    return out

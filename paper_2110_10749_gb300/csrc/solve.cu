@@ -1,0 +1,824 @@
+// Local boundary-integral solves, the Dirichlet-Neumann iteration and the
+// C ABI of the layer operators.  All Krylov and interface arithmetic is FP64
+// on the device; the host only sequences launches and reads one residual per
+// iteration.
+#include <math.h>
+#include <string.h>
+
+#include <functional>
+
+#include "internal.h"
+
+namespace ssd {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------ vector kernels
+constexpr int kDotThreads = 256;
+constexpr int kDotMaxBlocks = 120;
+
+// partial[v * nbx + bx] = sum over this block's chunk of V[v] . w
+__global__ void multidot_kernel(const double *V, int64_t ldv, const double *w, int64_t n, int64_t chunk,
+                                double *partial) {
+    __shared__ double red[kDotThreads];
+    const int v = blockIdx.y;
+    const double *a = V + (int64_t)v * ldv;
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    int64_t end = beg + chunk;
+    if (end > n) end = n;
+    double s = 0.0;
+    for (int64_t k = beg + threadIdx.x; k < end; k += kDotThreads) s += a[k] * w[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = kDotThreads / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void multidot_finish_kernel(const double *partial, int nbx, int nv, double *out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double s = 0.0;
+    for (int k = 0; k < nbx; ++k) s += partial[(int64_t)v * nbx + k];
+    out[v] = s;
+}
+
+// w += sign * sum_v coef[v] V[v]
+__global__ void vupdate_kernel(const double *V, int64_t ldv, int nv, const double *coef, double sign, double *w,
+                               int64_t n) {
+    __shared__ double c[130];
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) c[v] = sign * coef[v];
+    __syncthreads();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc = w[k];
+        for (int v = 0; v < nv; ++v) acc += c[v] * V[(int64_t)v * ldv + k];
+        w[k] = acc;
+    }
+}
+
+// y = a x + b y
+__global__ void axpby_kernel(int64_t n, double a, const double *x, double b, double *y) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        y[k] = a * x[k] + b * y[k];
+}
+
+// y = x * (1 / *d) (or y = x if *d == 0)
+__global__ void scale_inv_kernel(int64_t n, const double *x, const double *d, double *y) {
+    const double dd = *d;
+    const double f = dd != 0.0 ? 1.0 / dd : 1.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        y[k] = x[k] * f;
+}
+
+// y -= (*s) * f
+__global__ void sub_dev_scalar_kernel(int64_t n, const double *s, double f, double *y) {
+    const double v = (*s) * f;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        y[k] -= v;
+}
+
+// GMRES bookkeeping, one thread: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2),
+// previous rotations applied, new rotation formed, residual estimate updated.
+__global__ void givens_kernel(double *H, int ldh, double *cs, double *sn, double *g, const double *h1,
+                              const double *h2, const double *nrm2, int j, double *out) {
+    if (threadIdx.x != 0) return;
+    double *col = H + (int64_t)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+    const double hn = sqrt(fmax(*nrm2, 0.0));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    if (den == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+    } else {
+        cs[j] = col[j] / den;
+        sn[j] = col[j + 1] / den;
+    }
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    out[0] = fabs(g[j + 1]);
+    out[1] = hn;
+}
+
+// Back substitution H(0:k, 0:k) y = g(0:k), one thread.
+__global__ void backsolve_kernel(const double *H, int ldh, const double *g, int k, double *y) {
+    if (threadIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int l = i + 1; l < k; ++l) s -= H[(int64_t)l * ldh + i] * y[l];
+        y[i] = s / H[(int64_t)i * ldh + i];
+    }
+}
+
+__global__ void gmres_init_kernel(double *g, int m, const double *beta) {
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? *beta : 0.0;
+}
+
+__global__ void sqrt_kernel(double *v) {
+    if (threadIdx.x == 0) *v = sqrt(fmax(*v, 0.0));
+}
+
+// q_new = (1 - theta) q + theta (u . n)
+__global__ void q_update_kernel(int64_t n, double theta, const double *q, const double *u, const double *nrm,
+                                double *qn) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double un = u[i] * nrm[i] + u[n + i] * nrm[n + i] + u[2 * n + i] * nrm[2 * n + i];
+        qn[i] = (1.0 - theta) * q[i] + theta * un;
+    }
+}
+
+// BJS traction (eq. f): f = -p n + s (gamma/sqrt(kappa)) (u - (u.n) n)
+__global__ void traction_bjs_kernel(int64_t n, const double *p, const double *u, const double *nrm, double coef,
+                                    double *f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double n0 = nrm[i], n1 = nrm[n + i], n2 = nrm[2 * n + i];
+        double u0 = 0, u1 = 0, u2 = 0;
+        if (u) { u0 = u[i]; u1 = u[n + i]; u2 = u[2 * n + i]; }
+        const double un = u0 * n0 + u1 * n1 + u2 * n2;
+        f[i] = -p[i] * n0 + coef * (u0 - un * n0);
+        f[n + i] = -p[i] * n1 + coef * (u1 - un * n1);
+        f[2 * n + i] = -p[i] * n2 + coef * (u2 - un * n2);
+    }
+}
+
+// Porous-sphere benchmark traction (Section 7.3, eqs. f_r, f_theta): the
+// computed Darcy pressure plus the exact velocity-derivative terms,
+// f = (-p + 2 mu du_r/dr) e_r + f_theta e_theta, with sin(theta) e_theta =
+// cos(theta) e_r - e for the flow direction e and c = 2 + kappa/R^2:
+//   2 mu du_r/dr = -12 mu U kappa cos(theta) / (R^3 c),
+//   f_theta      = -(3 mu U/(R c)) (1 + 2 kappa/R^2) sin(theta).
+__global__ void traction_jt_kernel(int64_t n, const double *p, const double *xyz, double R, double kappa, double mu,
+                                   double U, double e0, double e1, double e2, double *f) {
+    const double c = 2.0 + kappa / (R * R);
+    const double bcoef = -(3.0 * mu * U / (R * c)) * (1.0 + 2.0 * kappa / (R * R));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = xyz[i], y = xyz[n + i], z = xyz[2 * n + i];
+        const double r = sqrt(x * x + y * y + z * z);
+        const double er0 = x / r, er1 = y / r, er2 = z / r;
+        const double ct = (e0 * x + e1 * y + e2 * z) / r;
+        const double a = -12.0 * mu * U * kappa * ct / (R * R * R * c);
+        const double fr = -p[i] + a;
+        f[i] = fr * er0 + bcoef * (ct * er0 - e0);
+        f[n + i] = fr * er1 + bcoef * (ct * er1 - e1);
+        f[2 * n + i] = fr * er2 + bcoef * (ct * er2 - e2);
+    }
+}
+
+// pn = p n
+__global__ void scalar_times_normal_kernel(int64_t n, const double *p, const double *nrm, double *pn) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) pn[k * n + i] = p[i] * nrm[k * n + i];
+}
+
+// tangential part u - (u . n) n
+__global__ void tangential_kernel(int64_t n, const double *u, const double *nrm, double *t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double un = u[i] * nrm[i] + u[n + i] * nrm[n + i] + u[2 * n + i] * nrm[2 * n + i];
+        for (int k = 0; k < 3; ++k) t[k * n + i] = u[k * n + i] - un * nrm[k * n + i];
+    }
+}
+
+inline unsigned grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// ------------------------------------------------------------------- helpers
+struct Buf {
+    ssd_ctx *ctx = nullptr;
+    void *p = nullptr;
+    Buf() {}
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    ~Buf() { if (ctx) dev_free(ctx, p); }
+    int alloc(ssd_ctx *c, size_t bytes) {
+        ctx = c;
+        return dev_alloc(c, bytes, &p);
+    }
+    double *d() const { return static_cast<double *>(p); }
+};
+
+struct Dots {
+    ssd_ctx *ctx;
+    cudaStream_t s;
+    Buf partial;
+    int init(ssd_ctx *c, cudaStream_t st, int maxv) {
+        ctx = c;
+        s = st;
+        return partial.alloc(c, sizeof(double) * kDotMaxBlocks * (maxv + 1));
+    }
+    // out[v] = V[v] . w, v < nv (deterministic)
+    int multi(const double *V, int64_t ldv, int nv, const double *w, int64_t n, double *out) {
+        int64_t nbx = (n + 4095) / 4096;
+        if (nbx > kDotMaxBlocks) nbx = kDotMaxBlocks;
+        if (nbx < 1) nbx = 1;
+        const int64_t chunk = (n + nbx - 1) / nbx;
+        multidot_kernel<<<dim3((unsigned)nbx, (unsigned)nv), kDotThreads, 0, s>>>(V, ldv, w, n, chunk,
+                                                                                  partial.d());
+        multidot_finish_kernel<<<(nv + 127) / 128, 128, 0, s>>>(partial.d(), (int)nbx, nv, out);
+        ctx->launches += 2;
+        return launch_check(ctx, "dot kernels");
+    }
+};
+
+int read_scalars(ssd_ctx *ctx, const double *dev, int k, double *host, cudaStream_t s) {
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(ctx->hbuf, dev, sizeof(double) * k, cudaMemcpyDeviceToHost, s),
+                       "scalar copy"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "stream sync"));
+    memcpy(host, ctx->hbuf, sizeof(double) * k);
+    return SSD_OK;
+}
+
+// ---------------------------------------------------------------------- GMRES
+typedef std::function<int(const double *in, double *out)> MatVec;
+
+struct GmresResult {
+    int iters = 0;
+    double relres = 1.0;
+};
+
+// Restarted GMRES (Saad) with classical Gram-Schmidt and one
+// reorthogonalisation (CGS2), x0 = 0 unless `warm`.  Stops when the residual
+// estimate falls to tol * ||b|| or after maxit Arnoldi steps.
+int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double *b, double *x, double tol,
+          int restart, int maxit, bool warm, GmresResult *res) {
+    const int m = restart;
+    Buf V, w, small;
+    SSD_TRY(V.alloc(ctx, sizeof(double) * (size_t)(m + 1) * n));
+    SSD_TRY(w.alloc(ctx, sizeof(double) * n));
+    const int ldh = m + 1;
+    // small: H[(m+1)*m], cs[m], sn[m], g[m+1], h1[m+1], h2[m+1], y[m], scal[8]
+    const size_t nsmall = (size_t)ldh * m + 2 * m + 3 * (m + 1) + m + 8;
+    SSD_TRY(small.alloc(ctx, sizeof(double) * nsmall));
+    double *H = small.d(), *cs = H + (size_t)ldh * m, *sn = cs + m, *g = sn + m, *h1 = g + m + 1,
+           *h2 = h1 + m + 1, *y = h2 + m + 1, *scal = y + m;
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, m + 1));
+    const unsigned gb = grid_for(n);
+
+    // ||b||
+    SSD_TRY(dots.multi(b, 0, 1, b, n, scal));
+    double hb[2];
+    SSD_TRY(read_scalars(ctx, scal, 1, hb, s));
+    const double bnorm = sqrt(hb[0]);
+    if (!isfinite(bnorm)) return set_error(ctx, SSD_ENUMERIC, "non-finite right-hand side");
+    if (!warm) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
+    res->iters = 0;
+    res->relres = 0.0;
+    if (bnorm == 0.0) {
+        SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
+        return SSD_OK;
+    }
+    int total = 0;
+    bool first = true;
+    for (;;) {
+        // r = b - A x  (r = b when x = 0 on the first cycle)
+        double *v0 = V.d();
+        if (first && !warm) {
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(v0, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                               "copy"));
+        } else {
+            SSD_TRY(A(x, v0));
+            axpby_kernel<<<gb, 256, 0, s>>>(n, 1.0, b, -1.0, v0);
+            ctx->launches++;
+        }
+        first = false;
+        SSD_TRY(dots.multi(v0, 0, 1, v0, n, scal));
+        sqrt_kernel<<<1, 32, 0, s>>>(scal);
+        gmres_init_kernel<<<1, 128, 0, s>>>(g, m, scal);
+        scale_inv_kernel<<<gb, 256, 0, s>>>(n, v0, scal, v0);
+        ctx->launches += 3;
+        SSD_TRY(read_scalars(ctx, scal, 1, hb, s));
+        double rel = hb[0] / bnorm;
+        res->relres = rel;
+        if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
+        if (rel <= tol || total >= maxit || hb[0] == 0.0) break;
+        int k = 0;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V.d() + (size_t)j * n;
+            SSD_TRY(A(vj, w.d()));
+            ++total;
+            SSD_TRY(dots.multi(V.d(), n, j + 1, w.d(), n, h1));
+            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h1, -1.0, w.d(), n);
+            ctx->launches++;
+            SSD_TRY(dots.multi(V.d(), n, j + 1, w.d(), n, h2));
+            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h2, -1.0, w.d(), n);
+            ctx->launches++;
+            SSD_TRY(dots.multi(w.d(), 0, 1, w.d(), n, scal + 2));
+            givens_kernel<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, h1, h2, scal + 2, j, scal);
+            scale_inv_kernel<<<gb, 256, 0, s>>>(n, w.d(), scal + 1, V.d() + (size_t)(j + 1) * n);
+            ctx->launches += 2;
+            SSD_TRY(launch_check(ctx, "arnoldi step"));
+            SSD_TRY(read_scalars(ctx, scal, 2, hb, s));
+            k = j + 1;
+            rel = hb[0] / bnorm;
+            res->relres = rel;
+            if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
+            if (rel <= tol || total >= maxit || hb[1] == 0.0) { done = true; break; }
+        }
+        backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+        vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, k, y, 1.0, x, n);
+        ctx->launches += 2;
+        SSD_TRY(launch_check(ctx, "gmres update"));
+        if (done && (rel <= tol || hb[1] == 0.0)) break;
+        if (total >= maxit) break;
+    }
+    res->iters = total;
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "gmres sync"));
+    if (res->relres > tol) return set_error(ctx, SSD_ENOTCONV, "GMRES reached its iteration limit");
+    return SSD_OK;
+}
+
+// Successive approximations x <- step(x) until ||x_k - x_{k-1}|| <= tol ||x_k||.
+int successive(ssd_ctx *ctx, cudaStream_t s, int64_t n, const std::function<int(const double *, double *)> &step,
+               double *x, double tol, int maxit, GmresResult *res) {
+    Buf xn, scal;
+    SSD_TRY(xn.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(scal.alloc(ctx, sizeof(double) * 4));
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, 2));
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
+    const unsigned gb = grid_for(n);
+    for (int it = 1; it <= maxit; ++it) {
+        SSD_TRY(step(x, xn.d()));
+        SSD_TRY(dots.multi(xn.d(), 0, 1, xn.d(), n, scal.d()));
+        axpby_kernel<<<gb, 256, 0, s>>>(n, 1.0, xn.d(), -1.0, x);   // x = xn - x
+        ctx->launches++;
+        SSD_TRY(dots.multi(x, 0, 1, x, n, scal.d() + 1));
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(x, xn.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                           "copy"));
+        double h[2];
+        SSD_TRY(read_scalars(ctx, scal.d(), 2, h, s));
+        const double rel = h[0] > 0 ? sqrt(h[1] / h[0]) : 0.0;
+        res->iters = it;
+        res->relres = rel;
+        if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite iterate");
+        if (rel <= tol) return SSD_OK;
+    }
+    return set_error(ctx, SSD_ENOTCONV, "successive approximations reached the iteration limit");
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
+    if (!kr) return set_error(ctx, SSD_EINVAL, "krylov settings are NULL");
+    if (!(kr->tol > 0.0) || !isfinite(kr->tol)) return set_error(ctx, SSD_EINVAL, "tolerance must be positive");
+    if (kr->maxit < 1) return set_error(ctx, SSD_EINVAL, "maxit must be >= 1");
+    if (!kr->use_sa && (kr->restart < 1 || kr->restart > 128))
+        return set_error(ctx, SSD_EINVAL, "restart must be in 1..128");
+    if (kr->prec != SSD_FP64 && kr->prec != SSD_FP32C) return set_error(ctx, SSD_EINVAL, "unknown precision");
+    return SSD_OK;
+}
+
+// ------------------------------------------------------------- local solves
+int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu, double kappa,
+                     const double *q, double *p, const ssd_krylov &kr, GmresResult *res, cudaStream_t s) {
+    const int64_t n = pts->n;
+    Buf b, scal;
+    SSD_TRY(b.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(scal.alloc(ctx, sizeof(double) * 2));
+    // b_D = (mu / kappa) L q  (eq. Darcy_final)
+    PairCall pc;
+    pc.op = OP_LSL; pc.prec = kr.prec; pc.delta = delta; pc.dens0 = q; pc.a_op = mu / kappa; pc.out = b.d();
+    SSD_TRY(pair_apply(ctx, L, pc, s));
+    int st;
+    if (kr.use_sa) {
+        // p <- p + D^L p + b, projected to zero weighted mean (eq. Darcy_BIEM_iter)
+        Dots dots;
+        SSD_TRY(dots.init(ctx, s, 1));
+        auto step = [&](const double *x, double *y) -> int {
+            PairCall a;
+            a.op = OP_LDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.xin = x; a.a_id = 1.0; a.a_op = 1.0;
+            a.out = y;
+            SSD_TRY(pair_apply(ctx, L, a, s));
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, b.d(), 1.0, y);
+            ctx->launches++;
+            SSD_TRY(dots.multi(pts->w, 0, 1, y, n, scal.d()));
+            sub_dev_scalar_kernel<<<grid_for(n), 256, 0, s>>>(n, scal.d(), 1.0 / L.wsum, y);
+            ctx->launches++;
+            return launch_check(ctx, "darcy sa step");
+        };
+        st = successive(ctx, s, n, step, p, kr.tol, kr.maxit, res);
+    } else {
+        // -D^L p + (w . p)/sum(w): nonsingular, same solution for consistent b
+        auto A = [&](const double *x, double *y) -> int {
+            PairCall a;
+            a.op = OP_LDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.a_op = -1.0;
+            a.rank1_weight_mean = true; a.out = y;
+            return pair_apply(ctx, L, a, s);
+        };
+        st = gmres(ctx, s, n, A, b.d(), p, kr.tol, kr.restart, kr.maxit, false, res);
+    }
+    if (st != SSD_OK && st != SSD_ENOTCONV) return st;
+    // zero weighted mean
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, 1));
+    SSD_TRY(dots.multi(pts->w, 0, 1, p, n, scal.d()));
+    sub_dev_scalar_kernel<<<grid_for(n), 256, 0, s>>>(n, scal.d(), 1.0 / L.wsum, p);
+    ctx->launches++;
+    SSD_TRY(launch_check(ctx, "darcy gauge"));
+    return st;
+}
+
+int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
+                      const double *f, const double uinf[3], double *u, const ssd_krylov &kr, GmresResult *res,
+                      cudaStream_t s) {
+    const int64_t n = pts->n;
+    Buf b;
+    SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
+    // b_S = U_inf - M f  (eq. Stokes_final)
+    PairCall pc;
+    pc.op = OP_SSL; pc.prec = kr.prec; pc.delta = delta; pc.mu = mu; pc.dens0 = f; pc.a_op = -1.0;
+    pc.add[0] = uinf[0]; pc.add[1] = uinf[1]; pc.add[2] = uinf[2]; pc.out = b.d();
+    SSD_TRY(pair_apply(ctx, L, pc, s));
+    if (kr.use_sa) {
+        // u <- D^S u + b (eq. Stokes_BIEM_iter)
+        auto step = [&](const double *x, double *y) -> int {
+            PairCall a;
+            a.op = OP_SDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.a_op = 1.0; a.out = y;
+            SSD_TRY(pair_apply(ctx, L, a, s));
+            axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, 1.0, b.d(), 1.0, y);
+            ctx->launches++;
+            return launch_check(ctx, "stokes sa step");
+        };
+        return successive(ctx, s, 3 * n, step, u, kr.tol, kr.maxit, res);
+    }
+    // (I - D^S) u  [+ n (w . (u.n))/sum(w) when deflating]
+    auto A = [&](const double *x, double *y) -> int {
+        PairCall a;
+        a.op = OP_SDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.xin = x; a.a_id = 1.0; a.a_op = -1.0;
+        a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
+        a.out = y;
+        return pair_apply(ctx, L, a, s);
+    };
+    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, false, res);
+}
+
+// Stokes step with the BJS slip at its own velocity: with f = -p n + c P u
+// (c = s gamma/sqrt(kappa), P u = u - (u.n) n), u = D^S u + U_inf - M f reads
+//   (I - D^S) u + c M(P u) = U_inf + M(p n);
+// the matvec is one fused single+double layer pass.
+int stokes_solve_bjs_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
+                          const double *p, const double uinf[3], double c, double *u, const ssd_krylov &kr,
+                          GmresResult *res, cudaStream_t s) {
+    const int64_t n = pts->n;
+    Buf b, tmp;
+    SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(tmp.alloc(ctx, sizeof(double) * 3 * n));
+    scalar_times_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, p, pts->nrm, tmp.d());
+    ctx->launches++;
+    PairCall pc;
+    pc.op = OP_SSL; pc.prec = kr.prec; pc.delta = delta; pc.mu = mu; pc.dens0 = tmp.d(); pc.a_op = 1.0;
+    pc.add[0] = uinf[0]; pc.add[1] = uinf[1]; pc.add[2] = uinf[2]; pc.out = b.d();
+    SSD_TRY(pair_apply(ctx, L, pc, s));
+    auto A = [&](const double *x, double *y) -> int {
+        tangential_kernel<<<grid_for(n), 256, 0, s>>>(n, x, pts->nrm, tmp.d());
+        ctx->launches++;
+        PairCall a;
+        a.op = OP_SSLDL; a.prec = kr.prec; a.delta = delta; a.mu = mu; a.dens0 = x; a.dens1 = tmp.d();
+        a.alpha = c; a.beta = -1.0; a.xin = x; a.a_id = 1.0; a.a_op = 1.0; a.out = y;
+        a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
+        return pair_apply(ctx, L, a, s);
+    };
+    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, false, res);
+}
+
+// ------------------------------------------------------------------ D-N solve
+struct Ddm {
+    ssd_ctx *ctx;
+    const ssd_points *pts;
+    const Layout *L;
+    ssd_ddm_params P;
+    cudaStream_t s;
+    int64_t n;
+    Buf f, scal;
+    std::vector<int> inner;   // (darcy, stokes) per sweep
+    int nonconv = 0;
+
+    // one sweep: (q, uprev) -> (qn, u); p and f are left in pbuf and f
+    int sweep(const double *q, const double *uprev, double *qn, double *u, double *p) {
+        GmresResult rd, rs;
+        int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s);
+        if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
+        SSD_TRY(st);
+        if (P.traction_mode == SSD_TRACTION_BJS && P.bjs_implicit) {
+            const double coef = P.bjs_sign * P.gamma / sqrt(P.kappa);
+            st = stokes_solve_bjs_impl(ctx, pts, *L, P.delta, P.mu, p, P.uinf, coef, u, P.inner, &rs, s);
+            if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
+            SSD_TRY(st);
+            traction_bjs_kernel<<<grid_for(n), 256, 0, s>>>(n, p, u, pts->nrm, coef, f.d());
+            q_update_kernel<<<grid_for(n), 256, 0, s>>>(n, P.theta, q, u, pts->nrm, qn);
+            ctx->launches += 2;
+            inner.push_back(rd.iters);
+            inner.push_back(rs.iters);
+            return launch_check(ctx, "implicit BJS sweep");
+        }
+        if (P.traction_mode == SSD_TRACTION_BJS) {
+            const double coef = P.bjs_sign * P.gamma / sqrt(P.kappa);
+            traction_bjs_kernel<<<grid_for(n), 256, 0, s>>>(n, p, P.gamma != 0.0 ? uprev : nullptr, pts->nrm, coef,
+                                                            f.d());
+        } else {
+            const double U = sqrt(P.uinf[0] * P.uinf[0] + P.uinf[1] * P.uinf[1] + P.uinf[2] * P.uinf[2]);
+            const double e0 = U > 0 ? P.uinf[0] / U : 0.0, e1 = U > 0 ? P.uinf[1] / U : 0.0,
+                         e2 = U > 0 ? P.uinf[2] / U : 1.0;
+            traction_jt_kernel<<<grid_for(n), 256, 0, s>>>(n, p, pts->xyz, P.radius, P.kappa, P.mu, U, e0, e1, e2,
+                                                           f.d());
+        }
+        ctx->launches++;
+        SSD_TRY(launch_check(ctx, "traction"));
+        st = stokes_solve_impl(ctx, pts, *L, P.delta, P.mu, f.d(), P.uinf, u, P.inner, &rs, s);
+        if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
+        SSD_TRY(st);
+        q_update_kernel<<<grid_for(n), 256, 0, s>>>(n, P.theta, q, u, pts->nrm, qn);
+        ctx->launches++;
+        inner.push_back(rd.iters);
+        inner.push_back(rs.iters);
+        return launch_check(ctx, "q update");
+    }
+};
+
+int check_ddm(ssd_ctx *ctx, const ssd_ddm_params *P) {
+    if (!P) return set_error(ctx, SSD_EINVAL, "parameters are NULL");
+    if (!finite_pos(P->mu) || !finite_pos(P->kappa) || !finite_pos(P->delta))
+        return set_error(ctx, SSD_EINVAL, "mu, kappa and delta must be positive");
+    if (!(P->theta > 0.0 && P->theta <= 1.0)) return set_error(ctx, SSD_EINVAL, "theta must be in (0, 1]");
+    if (!isfinite(P->gamma) || P->gamma < 0.0) return set_error(ctx, SSD_EINVAL, "gamma must be >= 0");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(P->uinf[k])) return set_error(ctx, SSD_EINVAL, "non-finite far-field velocity");
+    if (!finite_pos(P->tol_outer) || P->maxit_outer < 1) return set_error(ctx, SSD_EINVAL, "bad outer settings");
+    if (P->traction_mode != SSD_TRACTION_BJS && P->traction_mode != SSD_TRACTION_JOSEPH_TAO)
+        return set_error(ctx, SSD_EINVAL, "unknown traction mode");
+    if (P->traction_mode == SSD_TRACTION_BJS && !(P->bjs_sign == 1.0 || P->bjs_sign == -1.0))
+        return set_error(ctx, SSD_EINVAL, "bjs_sign must be +1 or -1");
+    if (P->traction_mode == SSD_TRACTION_JOSEPH_TAO && !finite_pos(P->radius))
+        return set_error(ctx, SSD_EINVAL, "radius must be positive");
+    return check_krylov(ctx, &P->inner);
+}
+
+int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, double *q_out, double *p_out,
+             double *u_out, double *f_out, double drag[3], int *outer_its, int *inner_its, double *res_hist,
+             cudaStream_t s) {
+    SSD_TRY(check_ddm(ctx, prm));
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    Ddm D;
+    D.ctx = ctx; D.pts = pts; D.L = lref.L; D.P = *prm; D.s = s; D.n = pts->n;
+    const int64_t n = pts->n;
+    const bool stacked = prm->traction_mode == SSD_TRACTION_BJS && prm->gamma != 0.0 && !prm->bjs_implicit;
+    const int64_t nz = stacked ? 4 * n : n;
+    SSD_TRY(D.f.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(D.scal.alloc(ctx, sizeof(double) * 8));
+    Buf z, zn, p, u, c;
+    SSD_TRY(z.alloc(ctx, sizeof(double) * 4 * n));
+    SSD_TRY(zn.alloc(ctx, sizeof(double) * 4 * n));
+    SSD_TRY(p.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(u.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(z.d(), 0, sizeof(double) * 4 * n, s), "memset"));
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, 2));
+    int its = 0;
+    int status = SSD_OK;
+    std::vector<double> hist;
+    if (!prm->outer_gmres) {
+        // relaxed sweeps; z = (q, u_prev) with u_prev kept in z + n
+        for (its = 1; its <= prm->maxit_outer; ++its) {
+            SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
+            SSD_TRY(dots.multi(zn.d(), 0, 1, zn.d(), n, D.scal.d()));
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, zn.d(), -1.0, z.d());   // z = qn - q
+            ctx->launches++;
+            SSD_TRY(dots.multi(z.d(), 0, 1, z.d(), n, D.scal.d() + 1));
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(z.d(), zn.d(), sizeof(double) * 4 * n, cudaMemcpyDeviceToDevice,
+                                                    s), "copy"));
+            double h[2];
+            SSD_TRY(read_scalars(ctx, D.scal.d(), 2, h, s));
+            const double res = h[0] > 0 ? sqrt(h[1] / h[0]) : 0.0;
+            hist.push_back(res);
+            if (!isfinite(res)) return set_error(ctx, SSD_ENUMERIC, "non-finite DDM residual");
+            if (res <= prm->tol_outer) break;
+        }
+        if (its > prm->maxit_outer) { its = prm->maxit_outer; status = SSD_ENOTCONV; }
+    } else {
+        // GMRES on (I - G) z = c, c = F(0)
+        SSD_TRY(c.alloc(ctx, sizeof(double) * 4 * n));
+        SSD_TRY(D.sweep(z.d(), z.d() + n, c.d(), c.d() + n, p.d()));
+        auto F = [&](const double *v, double *out) -> int {
+            // out = v - (F(v) - c); F(v) = (q_new, u) of one sweep from v
+            const double *uprev = stacked ? v + n : z.d() + n;   // z + n stays zero here
+            SSD_TRY(D.sweep(v, uprev, zn.d(), zn.d() + n, p.d()));
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(out, c.d(), sizeof(double) * nz, cudaMemcpyDeviceToDevice, s),
+                               "copy"));
+            axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, -1.0, zn.d(), 1.0, out);  // c - F(v)
+            axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, 1.0, v, 1.0, out);        // + v
+            ctx->launches += 2;
+            return launch_check(ctx, "outer matvec");
+        };
+        GmresResult gr;
+        const int m_out = prm->maxit_outer < 128 ? prm->maxit_outer : 128;
+        int st = gmres(ctx, s, nz, F, c.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr);
+        if (st == SSD_ENOTCONV) status = SSD_ENOTCONV;
+        else SSD_TRY(st);
+        its = gr.iters;
+        hist.push_back(gr.relres);
+        if (!stacked) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(z.d() + n, 0, sizeof(double) * 3 * n, s), "memset"));
+        // final sweep from the solution gives the returned fields
+        SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(z.d() + n, zn.d() + n, sizeof(double) * 3 * n,
+                                                cudaMemcpyDeviceToDevice, s), "copy"));
+    }
+    // outputs: q (the interface variable at convergence), p_D, u_S, f_S
+    if (q_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(q_out, z.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                                  "copy"));
+    if (p_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(p_out, p.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                                  "copy"));
+    if (u_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u_out, z.d() + n, sizeof(double) * 3 * n,
+                                                       cudaMemcpyDeviceToDevice, s), "copy"));
+    if (f_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(f_out, D.f.d(), sizeof(double) * 3 * n,
+                                                       cudaMemcpyDeviceToDevice, s), "copy"));
+    // drag = sum_x w f (eq. drag_int)
+    SSD_TRY(dots.multi(D.f.d(), n, 3, pts->w, n, D.scal.d()));
+    double dh[3];
+    SSD_TRY(read_scalars(ctx, D.scal.d(), 3, dh, s));
+    if (drag) for (int k = 0; k < 3; ++k) drag[k] = dh[k];
+    if (outer_its) *outer_its = its;
+    if (inner_its) {
+        const size_t cap = 2 * (size_t)(prm->maxit_outer + 2);
+        for (size_t k = 0; k < D.inner.size() && k < cap; ++k) inner_its[k] = D.inner[k];
+    }
+    if (res_hist)
+        for (size_t k = 0; k < hist.size() && k < (size_t)prm->maxit_outer; ++k) res_hist[k] = hist[k];
+    if (D.nonconv && status == SSD_OK) status = SSD_ENOTCONV;
+    if (status == SSD_ENOTCONV) set_error(ctx, SSD_ENOTCONV, "iteration limit reached in the D-N solve");
+    return status;
+}
+
+int op_entry(ssd_ctx *ctx, const ssd_points *pts, const PairCall &pc, cudaStream_t s) {
+    if (!finite_pos(pc.delta)) return set_error(ctx, SSD_EINVAL, "delta must be positive and finite");
+    if (!finite_pos(pc.mu)) return set_error(ctx, SSD_EINVAL, "mu must be positive and finite");
+    if (!isfinite(pc.alpha) || !isfinite(pc.beta)) return set_error(ctx, SSD_EINVAL, "non-finite alpha or beta");
+    if (pc.prec != SSD_FP64 && pc.prec != SSD_FP32C) return set_error(ctx, SSD_EINVAL, "unknown precision");
+    if (!pc.dens0 || !pc.out) return set_error(ctx, SSD_EINVAL, "NULL density or output");
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    return pair_apply(ctx, *lref.L, pc, s);
+}
+
+}  // namespace
+
+int dot(ssd_ctx *ctx, const double *a, const double *b, int64_t n, double *dev_out, cudaStream_t s) {
+    Dots d;
+    SSD_TRY(d.init(ctx, s, 1));
+    return d.multi(a, 0, 1, b, n, dev_out);
+}
+
+}  // namespace ssd
+
+using namespace ssd;
+
+extern "C" {
+
+int ssd_laplace_SL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *g, double *out, int prec,
+                   ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    PairCall pc;
+    pc.op = OP_LSL; pc.prec = prec; pc.delta = delta; pc.dens0 = g; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_laplace_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *p, double *out, int prec,
+                   ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    PairCall pc;
+    pc.op = OP_LDL; pc.prec = prec; pc.delta = delta; pc.dens0 = p; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_stokes_SL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, const double *f, double *out,
+                  int prec, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    PairCall pc;
+    pc.op = OP_SSL; pc.prec = prec; pc.delta = delta; pc.mu = mu; pc.dens0 = f; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_stokes_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u, double *out, int prec,
+                  ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    PairCall pc;
+    pc.op = OP_SDL; pc.prec = prec; pc.delta = delta; pc.dens0 = u; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_stokes_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, const double *f, const double *u,
+                    double alpha, double beta, double *out, int prec, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    if (!f) return set_error(ctx, SSD_EINVAL, "NULL traction");
+    PairCall pc;
+    pc.op = OP_SSLDL; pc.prec = prec; pc.delta = delta; pc.mu = mu; pc.dens0 = u; pc.dens1 = f;
+    pc.alpha = alpha; pc.beta = beta; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_laplace_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *g, const double *p,
+                     double alpha, double beta, double *out, int prec, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    if (!g) return set_error(ctx, SSD_EINVAL, "NULL single-layer density");
+    PairCall pc;
+    pc.op = OP_LSLDL; pc.prec = prec; pc.delta = delta; pc.dens0 = p; pc.dens1 = g;
+    pc.alpha = alpha; pc.beta = beta; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_darcy_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, double kappa, const double *q,
+                    double *p_out, const ssd_krylov *kr, int *iters, double *relres, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!finite_pos(delta) || !finite_pos(mu) || !finite_pos(kappa))
+        return set_error(ctx, SSD_EINVAL, "delta, mu and kappa must be positive");
+    if (!q || !p_out) return set_error(ctx, SSD_EINVAL, "NULL q or p");
+    SSD_TRY(check_krylov(ctx, kr));
+    cudaStream_t s = (cudaStream_t)stream;
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    GmresResult r;
+    const int st = darcy_solve_impl(ctx, pts, *lref.L, delta, mu, kappa, q, p_out, *kr, &r, s);
+    if (iters) *iters = r.iters;
+    if (relres) *relres = r.relres;
+    if (st == SSD_OK || st == SSD_ENOTCONV) cudaStreamSynchronize(s);
+    return st;
+}
+
+int ssd_stokes_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, const double *f,
+                     const double uinf[3], double *u_out, const ssd_krylov *kr, int *iters, double *relres,
+                     ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!finite_pos(delta) || !finite_pos(mu)) return set_error(ctx, SSD_EINVAL, "delta and mu must be positive");
+    if (!f || !u_out || !uinf) return set_error(ctx, SSD_EINVAL, "NULL f, u or uinf");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(uinf[k])) return set_error(ctx, SSD_EINVAL, "non-finite far-field velocity");
+    SSD_TRY(check_krylov(ctx, kr));
+    cudaStream_t s = (cudaStream_t)stream;
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    GmresResult r;
+    const int st = stokes_solve_impl(ctx, pts, *lref.L, delta, mu, f, uinf, u_out, *kr, &r, s);
+    if (iters) *iters = r.iters;
+    if (relres) *relres = r.relres;
+    if (st == SSD_OK || st == SSD_ENOTCONV) cudaStreamSynchronize(s);
+    return st;
+}
+
+int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, double *q, double *p_D,
+                  double *u_S, double *f_S, double drag[3], int *outer_its, int *inner_its, double *res_hist,
+                  ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    return ddm_impl(ctx, pts, prm, q, p_D, u_S, f_S, drag, outer_its, inner_its, res_hist, (cudaStream_t)stream);
+}
+
+int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double *nrm, const double *w,
+                       const ssd_ddm_params *prm, double *q, double *p_D, double *u_S, double *f_S, double drag[3],
+                       int *outer_its, int *inner_its, double *res_hist, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (n <= 0 || !xyz || !nrm || !w) return set_error(ctx, SSD_EINVAL, "bad host point arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    Buf dx, dn, dw, dout;
+    SSD_TRY(dx.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(dn.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(dw.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(dout.alloc(ctx, sizeof(double) * 8 * n));
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(dx.d(), xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s), "h2d"));
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(dn.d(), nrm, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s), "h2d"));
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(dw.d(), w, sizeof(double) * n, cudaMemcpyHostToDevice, s), "h2d"));
+    ssd_points pts;
+    pts.n = n; pts.xyz = dx.d(); pts.nrm = dn.d(); pts.w = dw.d(); pts.layout = nullptr;
+    SSD_TRY(ssd_points_prepare(ctx, &pts, stream));
+    double *o = dout.d();
+    const int st = ddm_impl(ctx, &pts, prm, o, o + n, o + 2 * n, o + 5 * n, drag, outer_its, inner_its, res_hist, s);
+    ssd_points_release(ctx, &pts);
+    if (st != SSD_OK && st != SSD_ENOTCONV) return st;
+    if (q) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(q, o, sizeof(double) * n, cudaMemcpyDeviceToHost, s), "d2h"));
+    if (p_D) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(p_D, o + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s), "d2h"));
+    if (u_S) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u_S, o + 2 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s),
+                                "d2h"));
+    if (f_S) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(f_S, o + 5 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s),
+                                "d2h"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "sync"));
+    return st;
+}
+
+}  // extern "C"

@@ -21,3 +21,17 @@ def read_golden(name):
             if line:
                 rows.append(line.split())
     return rows
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    """Built libssd and a context on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_10749_gb300 import build as _b
+    _b.build()
+    import paper_2110_10749_gb300 as ssd
+    ctx = ssd.Context(0)
+    yield ctx
+    ctx.close()

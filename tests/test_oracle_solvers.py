@@ -165,3 +165,27 @@ def test_ddm_bjs_mode_fixed_point(sph8):
     assert np.abs(rg["q"] - (rg["u"] * n).sum(0)).max() < 1e-8
     f = S.traction_bjs(sph8, rg["p"], rg["u"], 1.0, 0.5)
     assert np.abs(f - rg["f"]).max() < 1e-7
+
+
+def test_deflated_stokes_solve_converges_at_high_order():
+    # with the normal-mode rank-one term the Fig. 4 Stokes solve needs no
+    # projection: the zero-flux solution is the exact one
+    errs = []
+    for h in (1 / 8, 1 / 16):
+        p = Q.sphere_points(0.8, h)
+        u, sig = A.stokeslet(p["xyz"], [0.2, 0.0, 0.0], [1.0, 0.0, 0.0], 1.0)
+        f = np.einsum("ikn,kn->in", sig, p["nrm"])
+        us, its, _ = S.stokes_solve(p, 3 * h, 1.0, f, [0, 0, 0], tol=1e-11, deflate=True)
+        errs.append(S.rms(us - u))
+    assert errs[1] < 1e-4 and errs[0] / errs[1] > 16
+
+
+def test_implicit_bjs_reaches_the_lagged_fixed_point(sph8):
+    # both BJS treatments solve the same coupled equations; their fixed
+    # points coincide (kappa = 1, where the lagged sweeps converge)
+    kw = dict(mu=1.0, kappa=1.0, gamma=0.5, uinf=[0.2, 0.0, 1.0], theta=0.5, tol=1e-11, maxit=80)
+    rl = S.ddm_solve(sph8, 3 / 8, outer="sa", traction="bjs", **kw)
+    ri = S.ddm_solve(sph8, 3 / 8, outer="gmres", traction="bjs", bjs_implicit=True, deflate=True, **kw)
+    assert np.abs(rl["u"] - ri["u"]).max() < 1e-8
+    assert np.abs(rl["p"] - ri["p"]).max() < 1e-8
+    assert ri["outer_its"] < rl["outer_its"]
