@@ -177,7 +177,7 @@ typedef struct {
     double tol;    /* stop when ||b - A x|| <= tol ||b|| (GMRES estimate) or, for SA,
                       when ||x_k - x_{k-1}|| <= tol ||x_k|| */
     int maxit;     /* total iteration limit */
-    int restart;   /* GMRES restart length m (1..128) */
+    int restart;   /* GMRES restart length m (1..256) */
     int use_sa;    /* 1: successive approximations (eqs. Darcy_BIEM_iter,
                       Stokes_BIEM_iter) instead of GMRES */
     int prec;      /* enum ssd_precision of the pair sums */
@@ -265,6 +265,62 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
                        const double *w, const ssd_ddm_params *prm, double *q, double *p_D,
                        double *u_S, double *f_S, double drag[3], int *outer_its,
                        int *inner_its, double *res_hist, ssd_stream stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent surfaces (uneven point counts, one smoothing radius each)
+ * handled in one launch per operator application.  The caller concatenates
+ * the surfaces' point sets: surface s owns indices [offsets[s], offsets[s+1])
+ * of xyz[3][n_total], nrm[3][n_total], w[n_total].  Densities of a batched
+ * call are [nrhs][c][n_total] (c = 1 scalar, 3 vector): right-hand side r
+ * applies every surface's operator to its own part of block r.  The
+ * operators are those of the single-surface calls above, evaluated surface
+ * by surface; nothing couples two surfaces.
+ */
+typedef struct ssd_batch_layout ssd_batch_layout;
+typedef struct {
+    int32_t nsurf;
+    const int64_t *offsets;   /* host [nsurf + 1], offsets[0] = 0, increasing */
+    const double *delta;      /* host [nsurf], smoothing radius per surface */
+    const double *xyz;        /* device [3][n_total] */
+    const double *nrm;        /* device [3][n_total] */
+    const double *w;          /* device [n_total] */
+    ssd_batch_layout *layout; /* from ssd_batch_prepare (required by batched calls) */
+} ssd_batch;
+
+/* Build the batched layout: per-surface Morton order, padding to 512, FP32
+ * and FP64 copies, per-surface constants and the work-item tables of both
+ * precisions.  Synchronises `stream`. */
+int ssd_batch_prepare(ssd_ctx *ctx, ssd_batch *b /* host struct */, ssd_stream stream);
+int ssd_batch_release(ssd_ctx *ctx, ssd_batch *b /* host struct */);
+
+enum ssd_operator {
+    SSD_OP_LAPLACE_SL = 0, SSD_OP_LAPLACE_DL = 1, SSD_OP_STOKES_SL = 2,
+    SSD_OP_STOKES_DL = 3, SSD_OP_STOKES_SLDL = 4, SSD_OP_LAPLACE_SLDL = 5
+};
+/* One launch for every (surface, right-hand side): out = op(dens0[, dens1]).
+ * op: enum ssd_operator; for the fused operators dens0 is the double-layer
+ * density and dens1 the single-layer one, weighted alpha (SL) and beta (DL).
+ * nrhs in 1..16.  Asynchronous on `stream`. */
+int ssd_batch_apply(ssd_ctx *ctx, const ssd_batch *b, int op, int nrhs, double mu, double alpha,
+                    double beta, const double *dens0, const double *dens1, double *out, int prec,
+                    ssd_stream stream);
+
+/* Dirichlet-Neumann solves of every (surface, right-hand side), all advanced
+ * together: every operator application of the sweep is one batched launch,
+ * and the local and interface GMRES run per system (own Hessenberg matrix,
+ * Givens rotations and stopping test; converged systems are frozen) in one
+ * Krylov cycle (restart = maxit, at most 256).  prm->delta is ignored (the
+ * batch gives one per surface); prm->uinf is ignored (uinf[r] is the
+ * far-field velocity of right-hand side r).  Supported: interface GMRES
+ * (outer_gmres = 1) with JOSEPH_TAO traction, or BJS traction with gamma = 0
+ * or bjs_implicit = 1.  Outputs (device, [nrhs][c][n_total]): q, p_D (c = 1),
+ * u_S, f_S (c = 3); any may be NULL.  Host outputs [nrhs][nsurf]: outer
+ * iterations, final interface residual; drag [nrhs][nsurf][3].
+ * Synchronises `stream`. */
+int ssd_batch_ddm_solve(ssd_ctx *ctx, const ssd_batch *b, const ssd_ddm_params *prm, int nrhs,
+                        const double *uinf /* host [nrhs][3] */, double *q, double *p_D,
+                        double *u_S, double *f_S, double *drag, int *outer_its, double *relres,
+                        ssd_stream stream);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,9 @@ EXPORTS = [
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
     "ssd_stokes_SLDL", "ssd_laplace_SLDL",
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
+    "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
 ]
+OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 
 
 class SsdError(RuntimeError):
@@ -71,6 +73,15 @@ class CDdmParams(C.Structure):
                 ("delta", C.c_double), ("theta", C.c_double), ("tol_outer", C.c_double),
                 ("maxit_outer", C.c_int), ("outer_gmres", C.c_int), ("traction_mode", C.c_int),
                 ("bjs_implicit", C.c_int), ("bjs_sign", C.c_double), ("radius", C.c_double), ("inner", CKrylov)]
+
+
+class BatchLayoutC(C.Structure):
+    pass
+
+
+class CBatch(C.Structure):
+    _fields_ = [("nsurf", C.c_int32), ("offsets", C.POINTER(C.c_int64)), ("delta", C.POINTER(C.c_double)),
+                ("xyz", C.c_void_p), ("nrm", C.c_void_p), ("w", C.c_void_p), ("layout", C.POINTER(BatchLayoutC))]
 
 
 class CKernelStats(C.Structure):
@@ -120,6 +131,11 @@ def lib():
                           C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
         "ssd_ddm_solve_host": [P, i64, P, P, P, C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
                                C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
+        "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
+        "ssd_batch_release": [P, C.POINTER(CBatch)],
+        "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
+        "ssd_batch_ddm_solve": [P, C.POINTER(CBatch), C.POINTER(CDdmParams), i, C.POINTER(d), P, P, P, P,
+                                C.POINTER(d), C.POINTER(i), C.POINTER(d), P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -378,3 +394,75 @@ def ddm_solve_host(ctx, xyz, nrm, w, prm, out=None, raise_on_notconv=True):
     out["drag"] = np.array(drag[:])
     out["outer_its"] = oits.value
     return out
+
+
+class Batch:
+    """Many surfaces in one launch: concatenated (3, n_total) point arrays with
+    offsets[s] .. offsets[s+1] the points of surface s and one delta each."""
+
+    def __init__(self, xyz, nrm, w, offsets, delta):
+        torch = _torch()
+        self.xyz = xyz.to(dtype=torch.float64).contiguous()
+        self.nrm = nrm.to(dtype=torch.float64).contiguous()
+        self.w = w.to(dtype=torch.float64).contiguous()
+        self.offsets = (C.c_int64 * len(offsets))(*[int(v) for v in offsets])
+        self.delta = (C.c_double * len(delta))(*[float(v) for v in delta])
+        self.nsurf = len(delta)
+        self.n = int(self.w.numel())
+        assert len(offsets) == self.nsurf + 1 and int(offsets[-1]) == self.n
+        self.c = CBatch(self.nsurf, self.offsets, self.delta, _ptr(self.xyz), _ptr(self.nrm), _ptr(self.w), None)
+        self.ctx = None
+
+    @classmethod
+    def from_numpy(cls, point_sets, deltas, device="cuda"):
+        torch = _torch()
+        offs = np.concatenate([[0], np.cumsum([p["w"].size for p in point_sets])])
+        cat = lambda k: torch.as_tensor(np.ascontiguousarray(np.concatenate([p[k] for p in point_sets], axis=-1)),
+                                        device=device)
+        return cls(cat("xyz"), cat("nrm"), cat("w"), offs, deltas)
+
+    def prepare(self, ctx):
+        ctx.check(lib().ssd_batch_prepare(ctx.h, C.byref(self.c), _stream()), "ssd_batch_prepare")
+        self.ctx = ctx
+        return self
+
+    def release(self):
+        if self.ctx is not None and self.c.layout:
+            lib().ssd_batch_release(self.ctx.h, C.byref(self.c))
+        self.ctx = None
+
+
+def batch_apply(ctx, batch, op, dens0, dens1=None, mu=1.0, alpha=1.0, beta=1.0, prec=FP64, out=None):
+    """One launch of `op` for every surface and right-hand side; densities [nrhs][c][n_total]."""
+    nrhs = int(dens0.shape[0])
+    nc = 1 if op in (OP_LAPLACE_SL, OP_LAPLACE_DL, OP_LAPLACE_SLDL) else 3
+    if out is None:
+        out = _torch().empty((nrhs, nc, batch.n), dtype=_torch().float64, device=dens0.device)
+    ctx.check(lib().ssd_batch_apply(ctx.h, C.byref(batch.c), int(op), nrhs, float(mu), float(alpha), float(beta),
+                                    _ptr(dens0), _ptr(dens1), _ptr(out), int(prec), _stream()), "ssd_batch_apply")
+    return out
+
+
+def batch_ddm_solve(ctx, batch, prm, uinf, raise_on_notconv=True):
+    """D-N solves of every (surface, right-hand side); uinf is [nrhs][3]."""
+    torch = _torch()
+    uinf = np.asarray(uinf, dtype=np.float64).reshape(-1, 3)
+    nrhs = uinf.shape[0]
+    dev = batch.xyz.device
+    o = {"q": torch.empty((nrhs, 1, batch.n), dtype=torch.float64, device=dev),
+         "p": torch.empty((nrhs, 1, batch.n), dtype=torch.float64, device=dev),
+         "u": torch.empty((nrhs, 3, batch.n), dtype=torch.float64, device=dev),
+         "f": torch.empty((nrhs, 3, batch.n), dtype=torch.float64, device=dev)}
+    drag = (C.c_double * (3 * nrhs * batch.nsurf))()
+    its = (C.c_int * (nrhs * batch.nsurf))()
+    rel = (C.c_double * (nrhs * batch.nsurf))()
+    ui = (C.c_double * (3 * nrhs))(*uinf.ravel())
+    st = lib().ssd_batch_ddm_solve(ctx.h, C.byref(batch.c), C.byref(prm), nrhs, ui, _ptr(o["q"]), _ptr(o["p"]),
+                                   _ptr(o["u"]), _ptr(o["f"]), drag, its, rel, _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_batch_ddm_solve")
+    o["drag"] = np.array(drag[:]).reshape(nrhs, batch.nsurf, 3)
+    o["outer_its"] = np.array(its[:]).reshape(nrhs, batch.nsurf)
+    o["relres"] = np.array(rel[:]).reshape(nrhs, batch.nsurf)
+    o["status"] = st
+    return o

@@ -16,9 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssd.so")
-SOURCES = ["ctx.cu", "pair.cu", "quad.cu", "solve.cu"]
-HEADERS = ["internal.h", "series_coef.h", os.path.join("..", "..", "include", "ssd.h")]
+SOURCES = ["ctx.cu", "pair.cu", "quad.cu", "solve.cu", "batch.cu"]
+HEADERS = ["internal.h", "series_coef.h", "erfcx_coef.h", os.path.join("..", "..", "include", "ssd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS_EXTRA = []
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
 
@@ -41,12 +42,13 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
+    FLAGS_EXTRA.clear()
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *FLAGS_EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,6 +56,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
         return obj, r.stdout + r.stderr
 
+    # tile-shape overrides for tuning sweeps (see csrc/internal.h)
+    for key in ("SSD_TPB32", "SSD_MINCTA32"):
+        if os.environ.get(key):
+            FLAGS_EXTRA.append("-D%s=%d" % (key, int(os.environ[key])))
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(compile_one, SOURCES))
     if verbose:

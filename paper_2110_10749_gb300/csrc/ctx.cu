@@ -1,6 +1,7 @@
 // Context, errors, device memory pool, kernel timing and point layouts.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <cub/device/device_radix_sort.cuh>
@@ -176,6 +177,29 @@ __global__ void fill_layout_kernel(const double *xyz, const double *nrm, const d
     }
 }
 
+// Bounding box of each 32-point chunk of the sorted layout (real points only;
+// a chunk of padding gets the padding position as a degenerate box).
+__global__ void chunk_box_kernel(Layout L) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.n_pad / kChunk) return;
+    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+    bool any = false;
+    for (int k = 0; k < kChunk; ++k) {
+        const int64_t i = c * kChunk + k;
+        if (i >= L.n) break;
+        const float4 p = L.pos32[i];
+        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+        any = true;
+    }
+    if (!any) {
+        const float4 p = L.pos32[c * kChunk];
+        lo[0] = hi[0] = p.x; lo[1] = hi[1] = p.y; lo[2] = hi[2] = p.z;
+    }
+    L.cbox[2 * c] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    L.cbox[2 * c + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+}
+
 // fixed-order FP64 sum of the weights (one block)
 __global__ void wsum_kernel(const double *w, int64_t n, double *out) {
     __shared__ double red[256];
@@ -190,7 +214,245 @@ __global__ void wsum_kernel(const double *w, int64_t n, double *out) {
     if (threadIdx.x == 0) *out = red[0];
 }
 
+// ------------------------------------------------------------- batched layouts
+// key = surface index above a 30-bit Morton code of the position in the
+// batch's bounding box: sorting groups each surface's points in Morton order
+__global__ void batch_key_kernel(const double *xyz, int64_t n, const double *bb, const int32_t *esurf,
+                                 uint64_t *key, int32_t *idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        const double ext = bb[3 + k] - bb[k];
+        double f = ext > 0 ? (xyz[k * n + i] - bb[k]) / ext : 0.0;
+        f = fmin(fmax(f, 0.0), 1.0);
+        q[k] = (uint32_t)(f * 1023.0);
+    }
+    const uint32_t m = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    key[i] = ((uint64_t)esurf[i] << 30) | m;
+    idx[i] = (int32_t)i;
+}
+
+struct BatchFillArgs {
+    int32_t nsurf;
+    const int64_t *off, *cnt, *poff;   // device copies
+    const double *xyz, *nrm, *w;
+    int64_t n_total, n_pad_total;
+    const int32_t *sorted;             // sorted position -> caller index
+};
+
+__global__ void batch_fill_kernel(const BatchFillArgs a, Layout L) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_pad_total) return;
+    // surface owning padded index i (binary search over padded offsets)
+    int lo = 0, hi = a.nsurf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.poff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int64_t local = i - a.poff[lo];
+    const int64_t n = a.n_total;
+    if (local < a.cnt[lo]) {
+        const int32_t o = a.sorted[a.off[lo] + local];
+        const double x = a.xyz[o], y = a.xyz[n + o], z = a.xyz[2 * n + o];
+        const double ww = a.w[o];
+        const double wx = ww * a.nrm[o], wy = ww * a.nrm[n + o], wz = ww * a.nrm[2 * n + o];
+        L.perm[i] = o;
+        L.pos64[i] = d4{x, y, z, ww};
+        L.wn64[i] = d4{wx, wy, wz, 0.0};
+        L.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)ww);
+        L.wn32[i] = make_float4((float)wx, (float)wy, (float)wz, 0.f);
+    } else {
+        const double far = 1.0e4;
+        L.perm[i] = -1;
+        L.pos64[i] = d4{far, far, far, 0.0};
+        L.wn64[i] = d4{0.0, 0.0, 0.0, 0.0};
+        L.pos32[i] = make_float4((float)far, (float)far, (float)far, 0.f);
+        L.wn32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// chunk boxes of the batched layout; chunks never straddle surfaces because
+// every surface is padded to a multiple of kRowAlign
+__global__ void batch_chunk_box_kernel(Layout L) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.n_pad / kChunk) return;
+    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+    bool any = false;
+    for (int k = 0; k < kChunk; ++k) {
+        const int64_t i = c * kChunk + k;
+        if (L.perm[i] < 0) continue;
+        const float4 p = L.pos32[i];
+        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+        any = true;
+    }
+    if (!any) {
+        const float4 p = L.pos32[c * kChunk];
+        lo[0] = hi[0] = p.x; lo[1] = hi[1] = p.y; lo[2] = hi[2] = p.z;
+    }
+    L.cbox[2 * c] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    L.cbox[2 * c + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+}
+
+// weight sum per surface, fixed order (one block per surface)
+__global__ void batch_wsum_kernel(const double *w, const int64_t *off, double *out) {
+    __shared__ double red[256];
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) acc += w[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[s] = red[0];
+}
+
+__global__ void batch_esurf_kernel(const int64_t *off, int32_t nsurf, int64_t n, int32_t *esurf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsurf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    esurf[i] = lo;
+}
+
 }  // namespace
+
+void batch_layout_release(ssd_ctx *ctx, BatchLayout *B) {
+    if (B->block) dev_free(ctx, B->block);
+    for (int k = 0; k < 2; ++k) {
+        if (B->items[k]) dev_free(ctx, B->items[k]);
+    }
+    *B = BatchLayout();
+}
+
+int batch_layout_build(ssd_ctx *ctx, const ssd_batch *b, BatchLayout *B, cudaStream_t s) {
+    if (!b || b->nsurf < 1 || b->nsurf > (1 << 20) || !b->offsets || !b->delta)
+        return set_error(ctx, SSD_EINVAL, "bad batch description");
+    if (!b->xyz || !b->nrm || !b->w) return set_error(ctx, SSD_EINVAL, "NULL batch point array");
+    BatchLayout out;
+    out.nsurf = b->nsurf;
+    if (b->offsets[0] != 0) return set_error(ctx, SSD_EINVAL, "offsets[0] must be 0");
+    int64_t pacc = 0;
+    for (int k = 0; k < b->nsurf; ++k) {
+        const int64_t nk = b->offsets[k + 1] - b->offsets[k];
+        if (nk <= 0) return set_error(ctx, SSD_EINVAL, "every surface needs at least one point");
+        if (!(b->delta[k] > 0.0) || !isfinite(b->delta[k]))
+            return set_error(ctx, SSD_EINVAL, "delta must be positive per surface");
+        out.off.push_back(b->offsets[k]);
+        out.n.push_back(nk);
+        out.poff.push_back(pacc);
+        const int64_t np = ((nk + kRowAlign - 1) / kRowAlign) * kRowAlign;
+        out.n_pad.push_back(np);
+        out.delta.push_back(b->delta[k]);
+        pacc += np;
+    }
+    out.n_total = b->offsets[b->nsurf];
+    out.n_pad_total = pacc;
+    if (out.n_pad_total > (int64_t)0x7fffffff - 1024) return set_error(ctx, SSD_EINVAL, "batch too large");
+    const int64_t n = out.n_total, np = out.n_pad_total;
+    const int ns = out.nsurf;
+
+    size_t off = 0;
+    auto carve = [&](size_t bb) { size_t o = off; off += (bb + 255) & ~size_t(255); return o; };
+    const size_t o_perm = carve(sizeof(int32_t) * np), o_p32 = carve(sizeof(float4) * np),
+                 o_w32 = carve(sizeof(float4) * np), o_p64 = carve(sizeof(d4) * np),
+                 o_w64 = carve(sizeof(d4) * np), o_cb = carve(sizeof(float4) * 2 * (np / kChunk)),
+                 o_es = carve(sizeof(int32_t) * n), o_ws = carve(sizeof(double) * ns),
+                 o_sc = carve(sizeof(double) * ns), o_meta = carve(sizeof(int64_t) * (4 * ns + 1));
+    void *blk = nullptr;
+    SSD_TRY(dev_alloc(ctx, off, &blk));
+    char *bp = static_cast<char *>(blk);
+    out.block = blk;
+    out.L.n = np;   // the concatenated arrays as one padded set
+    out.L.n_pad = np;
+    out.L.perm = reinterpret_cast<int32_t *>(bp + o_perm);
+    out.L.pos32 = reinterpret_cast<float4 *>(bp + o_p32);
+    out.L.wn32 = reinterpret_cast<float4 *>(bp + o_w32);
+    out.L.pos64 = reinterpret_cast<d4 *>(bp + o_p64);
+    out.L.wn64 = reinterpret_cast<d4 *>(bp + o_w64);
+    out.L.cbox = reinterpret_cast<float4 *>(bp + o_cb);
+    out.elem_surf = reinterpret_cast<int32_t *>(bp + o_es);
+    out.d_wsum = reinterpret_cast<double *>(bp + o_ws);
+    out.d_selfc = reinterpret_cast<double *>(bp + o_sc);
+    int64_t *dmeta = reinterpret_cast<int64_t *>(bp + o_meta);   // off[ns+1], cnt[ns], poff[ns]
+    std::vector<int64_t> hmeta(4 * ns + 1, 0);
+    for (int k = 0; k <= ns; ++k) hmeta[k] = b->offsets[k];
+    for (int k = 0; k < ns; ++k) { hmeta[ns + 1 + k] = out.n[k]; hmeta[2 * ns + 1 + k] = out.poff[k]; }
+    std::vector<double> selfc(ns);
+    for (int k = 0; k < ns; ++k) selfc[k] = 16.0 / (3.0 * sqrt(M_PI) * out.delta[k]);
+    int st = cuda_check(ctx, cudaMemcpyAsync(dmeta, hmeta.data(), sizeof(int64_t) * hmeta.size(),
+                                             cudaMemcpyHostToDevice, s), "batch meta copy");
+    if (st == SSD_OK)
+        st = cuda_check(ctx, cudaMemcpyAsync(out.d_selfc, selfc.data(), sizeof(double) * ns,
+                                             cudaMemcpyHostToDevice, s), "batch self copy");
+    // sort by (surface, Morton)
+    void *tmp = nullptr;
+    if (st == SSD_OK) {
+        size_t cub_bytes = 0;
+        int nbits = 30;
+        while ((1 << (nbits - 30)) < ns) ++nbits;
+        cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, (const uint64_t *)nullptr, (uint64_t *)nullptr,
+                                        (const int32_t *)nullptr, (int32_t *)nullptr, (int)n, 0, nbits, s);
+        size_t t_off = 0;
+        auto tcarve = [&](size_t bb) { size_t o = t_off; t_off += (bb + 255) & ~size_t(255); return o; };
+        const size_t o_k0 = tcarve(sizeof(uint64_t) * n), o_k1 = tcarve(sizeof(uint64_t) * n);
+        const size_t o_i0 = tcarve(sizeof(int32_t) * n), o_i1 = tcarve(sizeof(int32_t) * n);
+        const size_t o_bb = tcarve(sizeof(double) * 6), o_cub = tcarve(cub_bytes);
+        st = dev_alloc(ctx, t_off, &tmp);
+        if (st == SSD_OK) {
+            char *tb = static_cast<char *>(tmp);
+            uint64_t *k0 = reinterpret_cast<uint64_t *>(tb + o_k0), *k1 = reinterpret_cast<uint64_t *>(tb + o_k1);
+            int32_t *i0 = reinterpret_cast<int32_t *>(tb + o_i0), *i1 = reinterpret_cast<int32_t *>(tb + o_i1);
+            double *bb = reinterpret_cast<double *>(tb + o_bb);
+            const unsigned gn = (unsigned)((n + 255) / 256);
+            batch_esurf_kernel<<<gn, 256, 0, s>>>(dmeta, ns, n, out.elem_surf);
+            bbox_kernel<<<1, 256, 0, s>>>(b->xyz, n, bb);
+            batch_key_kernel<<<gn, 256, 0, s>>>(b->xyz, n, bb, out.elem_surf, k0, i0);
+            ctx->launches += 3;
+            st = launch_check(ctx, "batch keys");
+            if (st == SSD_OK) {
+                cudaError_t e = cub::DeviceRadixSort::SortPairs(tb + o_cub, cub_bytes, k0, k1, i0, i1, (int)n, 0,
+                                                                nbits, s);
+                ctx->launches += 4;
+                st = cuda_check(ctx, e, "batch radix sort");
+            }
+            if (st == SSD_OK) {
+                BatchFillArgs fa;
+                fa.nsurf = ns; fa.off = dmeta; fa.cnt = dmeta + ns + 1; fa.poff = dmeta + 2 * ns + 1;
+                fa.xyz = b->xyz; fa.nrm = b->nrm; fa.w = b->w; fa.n_total = n; fa.n_pad_total = np;
+                fa.sorted = i1;
+                batch_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(fa, out.L);
+                batch_chunk_box_kernel<<<(unsigned)((np / kChunk + 127) / 128), 128, 0, s>>>(out.L);
+                batch_wsum_kernel<<<ns, 256, 0, s>>>(b->w, dmeta, out.d_wsum);
+                ctx->launches += 3;
+                st = launch_check(ctx, "batch fill");
+            }
+        }
+    }
+    out.wsum.resize(ns);
+    if (st == SSD_OK)
+        st = cuda_check(ctx, cudaMemcpyAsync(out.wsum.data(), out.d_wsum, sizeof(double) * ns,
+                                             cudaMemcpyDeviceToHost, s), "wsum copy");
+    if (st == SSD_OK) st = cuda_check(ctx, cudaStreamSynchronize(s), "batch layout sync");
+    if (tmp) dev_free(ctx, tmp);
+    if (st == SSD_OK) {
+        for (int k = 0; k < ns; ++k)
+            if (!(out.wsum[k] > 0.0)) { st = set_error(ctx, SSD_EINVAL, "surface weights must sum to > 0"); break; }
+    }
+    if (st == SSD_OK) st = pair_batch_items(ctx, &out, s);
+    if (st != SSD_OK) {
+        batch_layout_release(ctx, &out);
+        return st;
+    }
+    *B = out;
+    return SSD_OK;
+}
 
 int check_points(ssd_ctx *ctx, const ssd_points *pts) {
     if (!pts) return set_error(ctx, SSD_EINVAL, "points is NULL");
@@ -217,6 +479,7 @@ int build_layout(ssd_ctx *ctx, const ssd_points *pts, bool sort, Layout *L, cuda
     const size_t o_w32 = carve(sizeof(float4) * n_pad);
     const size_t o_p64 = carve(sizeof(d4) * n_pad);
     const size_t o_w64 = carve(sizeof(d4) * n_pad);
+    const size_t o_cb = carve(sizeof(float4) * 2 * (n_pad / kChunk));
     const size_t o_ws = carve(sizeof(double) * 8);
     void *blk = nullptr;
     SSD_TRY(dev_alloc(ctx, off, &blk));
@@ -230,6 +493,7 @@ int build_layout(ssd_ctx *ctx, const ssd_points *pts, bool sort, Layout *L, cuda
     out.wn32 = reinterpret_cast<float4 *>(b + o_w32);
     out.pos64 = reinterpret_cast<d4 *>(b + o_p64);
     out.wn64 = reinterpret_cast<d4 *>(b + o_w64);
+    out.cbox = reinterpret_cast<float4 *>(b + o_cb);
     double *dsum = reinterpret_cast<double *>(b + o_ws);
 
     int32_t *sorted = nullptr;
@@ -266,7 +530,8 @@ int build_layout(ssd_ctx *ctx, const ssd_points *pts, bool sort, Layout *L, cuda
         fill_layout_kernel<<<(unsigned)((n_pad + 255) / 256), 256, 0, s>>>(pts->xyz, pts->nrm, pts->w, n, n_pad,
                                                                           sorted, out);
         wsum_kernel<<<1, 256, 0, s>>>(pts->w, n, dsum);
-        ctx->launches += 2;
+        chunk_box_kernel<<<(unsigned)((n_pad / kChunk + 127) / 128), 128, 0, s>>>(out);
+        ctx->launches += 3;
         st = launch_check(ctx, "layout fill");
     }
     if (st == SSD_OK) st = cuda_check(ctx, cudaMemcpyAsync(ctx->hbuf, dsum, sizeof(double),
@@ -329,6 +594,11 @@ int ssd_ctx_create(ssd_ctx **out, int device) {
     ctx->num_sms = prop.multiProcessorCount;
     if (cudaMallocHost((void **)&ctx->hbuf, 4096) != cudaSuccess) { delete ctx; return SSD_ENOMEM; }
     if (pair_occupancy(ctx) != SSD_OK) { cudaFreeHost(ctx->hbuf); delete ctx; return SSD_ECUDA; }
+    // tuning knob: waves of resident CTAs in an FP32C pair-kernel grid
+    if (const char *w = getenv("SSD_PAIR_WAVES")) {
+        const int v = atoi(w);
+        if (v >= 1 && v <= 64) ctx->waves32 = v;
+    }
     *out = ctx;
     return SSD_OK;
 }
@@ -399,6 +669,28 @@ int ssd_points_release(ssd_ctx *ctx, ssd_points *pts) {
         release_layout(ctx, &pts->layout->L);
         delete pts->layout;
         pts->layout = nullptr;
+    }
+    return SSD_OK;
+}
+
+int ssd_batch_prepare(ssd_ctx *ctx, ssd_batch *b, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!b) return set_error(ctx, SSD_EINVAL, "batch is NULL");
+    if (b->layout) return set_error(ctx, SSD_EINVAL, "batch already has a layout");
+    ssd_batch_layout *lay = new ssd_batch_layout();
+    const int st = batch_layout_build(ctx, b, &lay->B, (cudaStream_t)stream);
+    if (st != SSD_OK) { delete lay; return st; }
+    b->layout = lay;
+    return SSD_OK;
+}
+
+int ssd_batch_release(ssd_ctx *ctx, ssd_batch *b) {
+    if (!ctx || !b) return SSD_EINVAL;
+    if (b->layout) {
+        batch_layout_release(ctx, &b->layout->B);
+        delete b->layout;
+        b->layout = nullptr;
     }
     return SSD_OK;
 }

@@ -13,11 +13,19 @@ namespace ssd {
 
 // ------------------------------------------------------------------ tiling
 constexpr int kTile = 128;          // sources staged in shared memory per step
-constexpr int kTPB32 = 128;         // threads per CTA, FP32C pair kernel
-constexpr int kTPT32 = 2;           // targets per thread, FP32C
+#ifndef SSD_TPB32
+#define SSD_TPB32 128
+#endif
+#ifndef SSD_MINCTA32
+#define SSD_MINCTA32 4
+#endif
+constexpr int kTPB32 = SSD_TPB32;         // threads per CTA, FP32C pair kernel
+constexpr int kMinCTA32 = SSD_MINCTA32;   // resident CTAs per SM the FP32C kernel is compiled for
+constexpr int kTPT32 = 4;           // targets per thread, FP32C (two packed f32x2 pairs)
+constexpr int kChunk = 32;          // sources per bounding-box chunk (near/far test per warp)
 constexpr int kTPB64 = 128;         // threads per CTA, FP64 pair kernel
 constexpr int kTPT64 = 1;           // targets per thread, FP64
-constexpr int kRowAlign = 256;      // n_pad is a multiple of this (>= every CTA target span)
+constexpr int kRowAlign = 512;      // n_pad is a multiple of this (>= every CTA target span)
 
 // Operators of the pair kernels.
 enum Op { OP_LSL = 0, OP_LDL = 1, OP_SSL = 2, OP_SDL = 3, OP_SSLDL = 4, OP_LSLDL = 5 };
@@ -33,6 +41,7 @@ struct Layout {
     float4 *wn32 = nullptr;    // (w nx, w ny, w nz, 0)
     d4 *pos64 = nullptr;       // (x, y, z, w)
     d4 *wn64 = nullptr;        // (w nx, w ny, w nz, 0)
+    float4 *cbox = nullptr;    // per 32-point chunk: [2 * c] = (lo x, y, z, 0), [2 * c + 1] = (hi ...)
     double wsum = 0.0;         // sum of weights (host copy)
     void *block = nullptr;     // single allocation backing the arrays
 };
@@ -53,6 +62,7 @@ struct ssd_ctx {
     int device = 0;
     int num_sms = 0;
     int occ32 = 1, occ64 = 1;  // resident CTAs per SM of the pair kernels
+    int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
     std::string err;
     // caching device allocator: blocks are reused in stream order
     struct Block { void *p; size_t bytes; bool used; };
@@ -121,6 +131,50 @@ struct PairCall {
 };
 int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s);
 int pair_occupancy(ssd_ctx *ctx);
+
+// ------------------------------------------------------------ batched layout
+// Many surfaces concatenated (caller order: surface s owns caller indices
+// [off[s], off[s] + n[s])); each surface is Morton-sorted and padded to
+// kRowAlign separately so no work item straddles two surfaces.
+struct BatchLayout {
+    int32_t nsurf = 0;
+    int64_t n_total = 0, n_pad_total = 0;
+    std::vector<int64_t> off, n, poff, n_pad;   // host copies
+    std::vector<double> delta, wsum;
+    Layout L;                 // concatenated padded arrays; L.perm maps to caller indices
+    int32_t *elem_surf = nullptr;   // [n_total] surface of each caller index
+    double *d_wsum = nullptr;       // [nsurf] weight sum per surface
+    double *d_selfc = nullptr;      // [nsurf] lim s1(rho)/(rho delta) at rho = 0, i.e. 16/(3 sqrt(pi) delta)
+    // work items and per-surface descriptors, FP32C (index 0) and FP64 (index 1)
+    void *items[2] = {nullptr, nullptr};
+    void *surfs[2] = {nullptr, nullptr};
+    void *consts[2] = {nullptr, nullptr};
+    int64_t nitems[2] = {0, 0};
+    int64_t ptotal[2] = {0, 0};     // sum over surfaces of nsplit * n_pad
+    void *block = nullptr;          // backing allocation of the device arrays above
+};
+
+}  // namespace ssd
+
+struct ssd_batch_layout {
+    ssd::BatchLayout B;
+};
+
+namespace ssd {
+
+int batch_layout_build(ssd_ctx *ctx, const ssd_batch *b, BatchLayout *B, cudaStream_t s);
+// work items and per-surface constants of both precisions (pair.cu)
+int pair_batch_items(ssd_ctx *ctx, BatchLayout *B, cudaStream_t s);
+void batch_layout_release(ssd_ctx *ctx, BatchLayout *B);
+// Batched pair sums: out[r][c][i] for right-hand side r < nrhs of every surface;
+// add[r][c] per right-hand side (nrhs <= kMaxRhs); other fields as in PairCall.
+constexpr int kMaxRhs = 16;
+struct BatchCall {
+    PairCall pc;
+    int nrhs = 1;
+    double add[kMaxRhs][3] = {};
+};
+int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cudaStream_t s);
 
 // Quadrature (quad.cu)
 int quadrature_points(ssd_ctx *ctx, const ssd_surface *surf, double h, double angle_deg, int64_t capacity,

@@ -18,8 +18,10 @@
 // transformation (Knuth's TwoSum), so the accumulated error does not grow
 // with the number of tiles.
 #include <math.h>
+#include <string.h>
 
 #include "internal.h"
+#include "erfcx_coef.h"
 #include "series_coef.h"
 
 namespace ssd {
@@ -65,6 +67,17 @@ template <> struct Prec<double> {
     }
 };
 
+// Work item of a batched launch: targets [tbase, tbase + span) against
+// sources [s_beg, s_end) of surface `surf`, written to partial split `split`.
+struct BItem {
+    int32_t tbase, s_beg, s_end, surf, split, pad0, pad1, pad2;
+};
+// Surface of a batched layout: padded range [poff, poff + n_pad), n_real real
+// points, pbase = sum over earlier surfaces of nsplit * n_pad (partial offset).
+struct BSurf {
+    int64_t poff, n_pad, n_real, pbase, nsplit, pad0, pad1, pad2;
+};
+
 template <typename R> struct Consts {
     R inv_d, inv_d2, inv_d3, inv_d5;
     R rfar2;      // (rho_far delta)^2
@@ -78,6 +91,12 @@ template <typename R> struct KArgs {
     int64_t chunk;       // sources per split (multiple of kTile)
     Consts<R> c;
     R *part;             // [split][NC][2 or 1][n_pad]
+    // batched mode (items != nullptr): blockIdx.x = work item, blockIdx.y = right-hand side
+    const BItem *items;
+    const BSurf *surfs;
+    const Consts<R> *consts;   // per surface
+    int64_t rec_stride;        // density records per right-hand side
+    int64_t part_stride;       // partial values per right-hand side
 };
 
 // Smoothed radial factors k1 = s1/r, k2 = s2/r^3, k3 = s3/r^3, k4 = s4/r^5
@@ -87,8 +106,11 @@ template <typename R, int OP>
 __device__ __forceinline__ void smooth(R r2, const Consts<R> &c, bool anyser, R &k1, R &k2, R &k3, R &k4) {
     typedef Prec<R> P;
     const R rinv = P::rsq(r2);
-    const R t = r2 * c.inv_d2;
-    const R rho = r2 * rinv * c.inv_d;
+    // clamp at the far threshold (FP32: t = 40, 1 - s_i < 2e-12; FP64: t = 64,
+    // 1 - s_i < 1e-21): keeps the polynomials finite for distant pairs
+    const R tmax = sizeof(R) == 4 ? R(40) : R(64);
+    const R t = fmin(r2 * c.inv_d2, tmax);
+    const R rho = fmin(r2 * rinv * c.inv_d, sizeof(R) == 4 ? R(6.324555320336759) : R(8));
     const R e = P::exp_(-t);
     const R er = P::erf_(rho);
     const R ce = c.cg * rho * e;
@@ -196,7 +218,29 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
     __shared__ V4 sm_d0[kTile];
     __shared__ V4 sm_d1[OpInfo<OP>::D1 ? kTile : 1];
 
-    const int64_t tbase = (int64_t)blockIdx.x * (TPB * TPT);
+    int64_t tbase, s_beg, s_end, part_base, pstride;
+    const V4 *d0 = a.d0, *d1 = a.d1;
+    Consts<R> c;
+    if (a.items) {
+        const BItem it = a.items[blockIdx.x];
+        const BSurf sf = a.surfs[it.surf];
+        tbase = it.tbase; s_beg = it.s_beg; s_end = it.s_end;
+        c = a.consts[it.surf];
+        d0 += blockIdx.y * a.rec_stride;
+        d1 += blockIdx.y * a.rec_stride;
+        constexpr int NSL = sizeof(Acc<R>) / sizeof(R);
+        part_base = blockIdx.y * a.part_stride + NC * NSL * sf.pbase + (int64_t)it.split * NC * NSL * sf.n_pad - sf.poff;
+        pstride = sf.n_pad;
+    } else {
+        tbase = (int64_t)blockIdx.x * (TPB * TPT);
+        s_beg = (int64_t)blockIdx.y * a.chunk;
+        s_end = s_beg + a.chunk;
+        if (s_end > a.n_pad) s_end = a.n_pad;
+        c = a.c;
+        constexpr int NSL = sizeof(Acc<R>) / sizeof(R);
+        part_base = (int64_t)blockIdx.y * NC * NSL * a.n_pad;
+        pstride = a.n_pad;
+    }
     R y[TPT][3], dt[TPT][3];
     Acc<R> acc[TPT][NC];
 #pragma unroll
@@ -204,21 +248,17 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         const int64_t i = tbase + threadIdx.x + t * TPB;   // < n_pad by construction
         const V4 p = a.pos[i];
         y[t][0] = p.x; y[t][1] = p.y; y[t][2] = p.z;
-        const V4 d = a.d0[i];
+        const V4 d = d0[i];
         dt[t][0] = d.x; dt[t][1] = d.y; dt[t][2] = d.z;
     }
-    const int64_t s_beg = (int64_t)blockIdx.y * a.chunk;
-    int64_t s_end = s_beg + a.chunk;
-    if (s_end > a.n_pad) s_end = a.n_pad;
-    const Consts<R> c = a.c;
 
     for (int64_t tile = s_beg; tile < s_end; tile += kTile) {
         __syncthreads();
         for (int k = threadIdx.x; k < kTile; k += TPB) {
             sm_pos[k] = a.pos[tile + k];
             if (OpInfo<OP>::WN) sm_wn[k] = a.wn[tile + k];
-            sm_d0[k] = a.d0[tile + k];
-            if (OpInfo<OP>::D1) sm_d1[k] = a.d1[tile + k];
+            sm_d0[k] = d0[tile + k];
+            if (OpInfo<OP>::D1) sm_d1[k] = d1[tile + k];
         }
         __syncthreads();
         R part[TPT][3];
@@ -267,9 +307,299 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         const int64_t i = tbase + threadIdx.x + t * TPB;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            R *dst = a.part + (((int64_t)blockIdx.y * NC + q) * NS) * a.n_pad + i;
+            R *dst = a.part + part_base + (int64_t)(q * NS) * pstride + i;
             dst[0] = acc[t][q].hi;
-            if (NS == 2) dst[a.n_pad] = reinterpret_cast<const R *>(&acc[t][q])[1];
+            if (NS == 2) dst[pstride] = reinterpret_cast<const R *>(&acc[t][q])[1];
+        }
+    }
+}
+
+// --------------------------------------------------------- FP32C kernel (v2)
+// Four targets per thread, held as two packed f32x2 pairs so that every
+// target-dependent FP32 operation of the bare-kernel path issues as one
+// FFMA2/FADD2/FMUL2 for two targets.  Each warp tests its targets' bounding
+// box against the bounding box of every 32-source chunk: a chunk farther
+// than rho_far*delta from all of them runs the bare kernels with no per-source
+// test; otherwise each source is voted on as in the generic kernel, and the
+// smoothed path runs (scalar, per target) only when a target of the warp is
+// within rho_far*delta of it.
+struct K32Args {
+    const float4 *pos, *wn, *d0, *d1;
+    const float4 *cbox;
+    int64_t n, n_pad, chunk;
+    Consts<float> c;
+    float *part;
+    // batched mode (items != nullptr): blockIdx.x = work item, blockIdx.y = right-hand side
+    const BItem *items;
+    const BSurf *surfs;
+    const Consts<float> *consts;
+    int64_t rec_stride, part_stride;
+};
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rsq2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+
+// Packed pair terms for the target pair (dt = target densities) with the
+// displacement (dx, dy, dz) = y - x and r2 = |y - x|^2 already formed.
+// NEAR = false: bare kernels (s_i = 1).  NEAR = true: smoothed kernels written
+// as s_i = 1 - E_i, E_i = e^{-t} (erfcx(rho) - (2/sqrt(pi)) rho Q_i(t)),
+// t = rho^2, valid for rho >= 0.5 (the Taylor branch covers smaller rho);
+// Q_1 = (5 - 2t)/3, Q_2 = (2t - 3)/3, Q_3 = (-4t^2 + 14t - 3)/3,
+// Q_4 = -(8t^3 - 36t^2 + 6t + 9)/9 (Section 5.3).
+template <int OP, bool NEAR>
+__device__ __forceinline__ void pair2(const float2 dx, const float2 dy, const float2 dz, const float2 r2,
+                                      const float2 dt[3], const float4 &sw, const float4 &s0, const float4 &s1,
+                                      const Consts<float> &c, float2 acc[3]) {
+    const float2 ri = rsq2(r2);
+    const float2 ri2 = mul2(ri, ri);
+    const float2 ri3 = mul2(ri2, ri);
+    float2 k1 = ri, k2 = ri3, k3 = ri3, k4 = mul2(ri3, ri2);
+    if (NEAR) {
+        // t and rho clamped at t = 40 (e^{-t} < 5e-18): beyond it E_i is zero
+        // to FP32 precision, and the clamp keeps the Q_i polynomials finite
+        // for distant sources (zero-weight padding lies 1e4 away)
+        const float2 tr = mul2(r2, bc2(c.inv_d2));
+        const float2 t = make_float2(fminf(tr.x, 40.f), fminf(tr.y, 40.f));
+        const float2 rr = mul2(mul2(r2, ri), bc2(c.inv_d));
+        const float2 rho = make_float2(fminf(rr.x, 6.32455532f), fminf(rr.y, 6.32455532f));
+        const float2 et = mul2(t, bc2(-1.4426950408889634f));
+        const float2 e = make_float2(exp2f(et.x), exp2f(et.y));
+        const float2 w = fma2(make_float2(__fdividef(1.f, 1.f + rho.x), __fdividef(1.f, 1.f + rho.y)),
+                              bc2(kErfcxA), bc2(-kErfcxB));
+        const float2 P = erfcx_fit2(w);
+        const float2 cr = mul2(rho, bc2(c.cg));
+        const float third = 1.f / 3.f;
+        if (OpInfo<OP>::SL) {
+            const float2 q1 = fma2(t, bc2(-2.f * third), bc2(5.f * third));
+            const float2 q3 = fma2(fma2(t, bc2(-4.f * third), bc2(14.f * third)), t, bc2(-1.f));
+            k1 = mul2(k1, fma2(e, fma2(cr, q1, make_float2(-P.x, -P.y)), bc2(1.f)));
+            k3 = mul2(k3, fma2(e, fma2(cr, q3, make_float2(-P.x, -P.y)), bc2(1.f)));
+        }
+        if (OP == OP_LDL || OP == OP_LSLDL) {
+            const float2 q2 = fma2(t, bc2(2.f * third), bc2(-1.f));
+            k2 = mul2(k2, fma2(e, fma2(cr, q2, make_float2(-P.x, -P.y)), bc2(1.f)));
+        }
+        if (OP == OP_SDL || OP == OP_SSLDL) {
+            const float ninth = 1.f / 9.f;
+            const float2 q4 = fma2(fma2(fma2(t, bc2(-8.f * ninth), bc2(4.f)), t, bc2(-6.f * ninth)), t, bc2(-1.f));
+            k4 = mul2(k4, fma2(e, fma2(cr, q4, make_float2(-P.x, -P.y)), bc2(1.f)));
+        }
+    }
+    if (OP == OP_LSL) {
+        acc[0] = fma2(bc2(s0.x), k1, acc[0]);
+    } else if (OP == OP_LDL || OP == OP_LSLDL) {
+        const float2 yn = fma2(dz, bc2(sw.z), fma2(dy, bc2(sw.y), mul2(dx, bc2(sw.x))));
+        const float2 dp = sub2(bc2(s0.x), dt[0]);
+        acc[0] = fma2(mul2(dp, yn), k2, acc[0]);
+        if (OP == OP_LSLDL) acc[0] = fma2(bc2(s0.y), k1, acc[0]);
+    } else if (OP == OP_SSL) {
+        const float2 yf = fma2(dz, bc2(s0.z), fma2(dy, bc2(s0.y), mul2(dx, bc2(s0.x))));
+        const float2 b = mul2(yf, k3);
+        acc[0] = fma2(bc2(s0.x), k1, fma2(dx, b, acc[0]));
+        acc[1] = fma2(bc2(s0.y), k1, fma2(dy, b, acc[1]));
+        acc[2] = fma2(bc2(s0.z), k1, fma2(dz, b, acc[2]));
+    } else {  // OP_SDL, OP_SSLDL
+        const float2 ux = sub2(bc2(s0.x), dt[0]), uy = sub2(bc2(s0.y), dt[1]), uz = sub2(bc2(s0.z), dt[2]);
+        const float2 du = fma2(uz, dz, fma2(uy, dy, mul2(ux, dx)));
+        const float2 yn = fma2(dz, bc2(sw.z), fma2(dy, bc2(sw.y), mul2(dx, bc2(sw.x))));
+        float2 b = mul2(mul2(du, yn), k4);
+        if (OP == OP_SSLDL) {
+            const float2 yf = fma2(dz, bc2(s1.z), fma2(dy, bc2(s1.y), mul2(dx, bc2(s1.x))));
+            b = fma2(yf, k3, b);
+            acc[0] = fma2(bc2(s1.x), k1, acc[0]);
+            acc[1] = fma2(bc2(s1.y), k1, acc[1]);
+            acc[2] = fma2(bc2(s1.z), k1, acc[2]);
+        }
+        acc[0] = fma2(b, dx, acc[0]);
+        acc[1] = fma2(b, dy, acc[1]);
+        acc[2] = fma2(b, dz, acc[2]);
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args a) {
+    constexpr int NC = OpInfo<OP>::NC;
+    constexpr int NP = kTPT32 / 2;   // packed pairs per thread
+    __shared__ float4 sm_pos[kTile];
+    __shared__ float4 sm_wn[OpInfo<OP>::WN ? kTile : 1];
+    __shared__ float4 sm_d0[kTile];
+    __shared__ float4 sm_d1[OpInfo<OP>::D1 ? kTile : 1];
+
+    int64_t tbase, s_beg, s_end, part_base, pstride, nreal_end;
+    const float4 *d0 = a.d0, *d1 = a.d1;
+    Consts<float> c;
+    if (a.items) {
+        const BItem it = a.items[blockIdx.x];
+        const BSurf sf = a.surfs[it.surf];
+        tbase = it.tbase; s_beg = it.s_beg; s_end = it.s_end;
+        nreal_end = sf.poff + sf.n_real;
+        c = a.consts[it.surf];
+        d0 += blockIdx.y * a.rec_stride;
+        d1 += blockIdx.y * a.rec_stride;
+        part_base = blockIdx.y * a.part_stride + NC * 2 * sf.pbase + (int64_t)it.split * NC * 2 * sf.n_pad - sf.poff;
+        pstride = sf.n_pad;
+    } else {
+        tbase = (int64_t)blockIdx.x * (kTPB32 * kTPT32);
+        s_beg = (int64_t)blockIdx.y * a.chunk;
+        s_end = s_beg + a.chunk;
+        if (s_end > a.n_pad) s_end = a.n_pad;
+        nreal_end = a.n;
+        c = a.c;
+        part_base = (int64_t)blockIdx.y * NC * 2 * a.n_pad;
+        pstride = a.n_pad;
+    }
+    // target t = 2k + j (pair k, lane j) is index tbase + threadIdx.x + t * kTPB32
+    float2 y[NP][3], dt[NP][3];
+    float blo[3] = {1e30f, 1e30f, 1e30f}, bhi[3] = {-1e30f, -1e30f, -1e30f};
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int64_t i0 = tbase + threadIdx.x + (2 * k) * kTPB32, i1 = i0 + kTPB32;
+        const float4 p0 = a.pos[i0], p1 = a.pos[i1];
+        const float4 e0 = d0[i0], e1 = d0[i1];
+        y[k][0] = make_float2(p0.x, p1.x); y[k][1] = make_float2(p0.y, p1.y); y[k][2] = make_float2(p0.z, p1.z);
+        dt[k][0] = make_float2(e0.x, e1.x); dt[k][1] = make_float2(e0.y, e1.y); dt[k][2] = make_float2(e0.z, e1.z);
+        if (i0 < nreal_end) {
+            blo[0] = fminf(blo[0], p0.x); blo[1] = fminf(blo[1], p0.y); blo[2] = fminf(blo[2], p0.z);
+            bhi[0] = fmaxf(bhi[0], p0.x); bhi[1] = fmaxf(bhi[1], p0.y); bhi[2] = fmaxf(bhi[2], p0.z);
+        }
+        if (i1 < nreal_end) {
+            blo[0] = fminf(blo[0], p1.x); blo[1] = fminf(blo[1], p1.y); blo[2] = fminf(blo[2], p1.z);
+            bhi[0] = fmaxf(bhi[0], p1.x); bhi[1] = fmaxf(bhi[1], p1.y); bhi[2] = fmaxf(bhi[2], p1.z);
+        }
+    }
+    // warp bounding box of its real targets
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            blo[q] = fminf(blo[q], __shfl_xor_sync(0xffffffffu, blo[q], off));
+            bhi[q] = fmaxf(bhi[q], __shfl_xor_sync(0xffffffffu, bhi[q], off));
+        }
+    const bool warp_empty = blo[0] > bhi[0];
+    float hi[kTPT32][NC], lo[kTPT32][NC];
+#pragma unroll
+    for (int t = 0; t < kTPT32; ++t)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hi[t][q] = lo[t][q] = 0.f;
+
+    for (int64_t tile = s_beg; tile < s_end; tile += kTile) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < kTile; k += kTPB32) {
+            sm_pos[k] = a.pos[tile + k];
+            if (OpInfo<OP>::WN) sm_wn[k] = a.wn[tile + k];
+            sm_d0[k] = d0[tile + k];
+            if (OpInfo<OP>::D1) sm_d1[k] = d1[tile + k];
+        }
+        __syncthreads();
+        float2 part[NP][3];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) part[k][0] = part[k][1] = part[k][2] = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < kTile / kChunk; ++ch) {
+            const int64_t cidx = (tile + ch * kChunk) / kChunk;
+            const float4 clo = a.cbox[2 * cidx], chi = a.cbox[2 * cidx + 1];
+            const float gx = fmaxf(0.f, fmaxf(clo.x - bhi[0], blo[0] - chi.x));
+            const float gy = fmaxf(0.f, fmaxf(clo.y - bhi[1], blo[1] - chi.y));
+            const float gz = fmaxf(0.f, fmaxf(clo.z - bhi[2], blo[2] - chi.z));
+            const bool far_chunk = warp_empty || (gx * gx + gy * gy + gz * gz >= c.rfar2);
+            const int j0 = ch * kChunk;
+            if (far_chunk) {
+#pragma unroll 4
+                for (int j = j0; j < j0 + kChunk; ++j) {
+                    const float4 sp = sm_pos[j];
+                    const float4 sw = OpInfo<OP>::WN ? sm_wn[j] : sp;
+                    const float4 s0 = sm_d0[j];
+                    const float4 s1 = OpInfo<OP>::D1 ? sm_d1[j] : s0;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        const float2 dx = sub2(y[k][0], bc2(sp.x)), dy = sub2(y[k][1], bc2(sp.y)),
+                                     dz = sub2(y[k][2], bc2(sp.z));
+                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                        pair2<OP, false>(dx, dy, dz, r2, dt[k], sw, s0, s1, c, part[k]);
+                    }
+                }
+            } else {
+                for (int j = j0; j < j0 + kChunk; ++j) {
+                    const float4 sp = sm_pos[j];
+                    const float4 sw = OpInfo<OP>::WN ? sm_wn[j] : sp;
+                    const float4 s0 = sm_d0[j];
+                    const float4 s1 = OpInfo<OP>::D1 ? sm_d1[j] : s0;
+                    bool nearv = false, serv = false;
+                    float2 DX[NP], DY[NP], DZ[NP], R2[NP];
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        DX[k] = sub2(y[k][0], bc2(sp.x));
+                        DY[k] = sub2(y[k][1], bc2(sp.y));
+                        DZ[k] = sub2(y[k][2], bc2(sp.z));
+                        R2[k] = fma2(DZ[k], DZ[k], fma2(DY[k], DY[k], mul2(DX[k], DX[k])));
+                        nearv |= (R2[k].x < c.rfar2) | (R2[k].y < c.rfar2);
+                        serv |= (R2[k].x * c.inv_d2 < c.tser) | (R2[k].y * c.inv_d2 < c.tser);
+                    }
+                    if (__any_sync(0xffffffffu, serv)) {
+                        // a target of the warp is within 0.5 delta of this source
+                        // (the self pair or a close neighbour): scalar path with
+                        // the Taylor branch
+                        const int64_t js = tile + j;
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) {
+#pragma unroll
+                            for (int l = 0; l < 2; ++l) {
+                                const float dv[3] = {l ? DX[k].y : DX[k].x, l ? DY[k].y : DY[k].x,
+                                                     l ? DZ[k].y : DZ[k].x};
+                                const float rr = l ? R2[k].y : R2[k].x;
+                                const float dd[3] = {l ? dt[k][0].y : dt[k][0].x, l ? dt[k][1].y : dt[k][1].x,
+                                                     l ? dt[k][2].y : dt[k][2].x};
+                                const bool self = (js == tbase + threadIdx.x + (2 * k + l) * kTPB32);
+                                float accs[3] = {0.f, 0.f, 0.f};
+                                if (rr < c.rfar2)
+                                    pair_term<float, OP, true>(dv, rr, dd, sw, s0, s1, c, true, self, accs);
+                                else
+                                    pair_term<float, OP, false>(dv, rr, dd, sw, s0, s1, c, false, false, accs);
+                                if (l) {
+                                    part[k][0].y += accs[0]; part[k][1].y += accs[1]; part[k][2].y += accs[2];
+                                } else {
+                                    part[k][0].x += accs[0]; part[k][1].x += accs[1]; part[k][2].x += accs[2];
+                                }
+                            }
+                        }
+                    } else if (__any_sync(0xffffffffu, nearv)) {
+#pragma unroll
+                        for (int k = 0; k < NP; ++k)
+                            pair2<OP, true>(DX[k], DY[k], DZ[k], R2[k], dt[k], sw, s0, s1, c, part[k]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < NP; ++k)
+                            pair2<OP, false>(DX[k], DY[k], DZ[k], R2[k], dt[k], sw, s0, s1, c, part[k]);
+                    }
+                }
+            }
+        }
+        // fold the tile's partial sums into the two-float accumulators (TwoSum)
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    const int t = 2 * k + l;
+                    const float p = l ? part[k][q].y : part[k][q].x;
+                    const float sum = hi[t][q] + p;
+                    const float bp = sum - hi[t][q];
+                    lo[t][q] += (hi[t][q] - (sum - bp)) + (p - bp);
+                    hi[t][q] = sum;
+                }
+    }
+#pragma unroll
+    for (int t = 0; t < kTPT32; ++t) {
+        const int64_t i = tbase + threadIdx.x + t * kTPB32;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            float *dst = a.part + part_base + (int64_t)(q * 2) * pstride + i;
+            dst[0] = hi[t][q];
+            dst[pstride] = lo[t][q];
         }
     }
 }
@@ -365,6 +695,8 @@ struct EpiArgs {
 };
 
 __global__ void epilogue_kernel(const EpiArgs a) {
+    // one thread per (point, component): partial sums are summed over the
+    // splits in a fixed order in FP64
     __shared__ double extra, rank1;
     if (threadIdx.x == 0) {
         double e = a.add_dev ? *a.add_dev : 0.0;
@@ -379,51 +711,62 @@ __global__ void epilogue_kernel(const EpiArgs a) {
         rank1 = r1;
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_pad) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n_pad * a.nc) return;
+    const int q = (int)(g / a.n_pad);
+    const int64_t i = g - (int64_t)q * a.n_pad;
     const int32_t o = a.perm[i];
     if (o < 0) return;
-    for (int q = 0; q < a.nc; ++q) {
-        double s = 0.0;
-        for (int sp = 0; sp < a.nsplit; ++sp) {
-            const int64_t base = (((int64_t)sp * a.nc + q) * a.nslot) * a.n_pad + i;
-            if (a.part_is_float) {
-                const float *pf = reinterpret_cast<const float *>(a.part);
-                s += (double)pf[base];
-                if (a.nslot == 2) s += (double)pf[base + a.n_pad];
-            } else {
-                s += reinterpret_cast<const double *>(a.part)[base];
-            }
+    double s = 0.0;
+    for (int sp = 0; sp < a.nsplit; ++sp) {
+        const int64_t base = (((int64_t)sp * a.nc + q) * a.nslot) * a.n_pad + i;
+        if (a.part_is_float) {
+            const float *pf = reinterpret_cast<const float *>(a.part);
+            s += (double)pf[base];
+            if (a.nslot == 2) s += (double)pf[base + a.n_pad];
+        } else {
+            s += reinterpret_cast<const double *>(a.part)[base];
         }
-        double v = a.scale * s;
-        if (a.self_src) v += a.self_coef * a.pos64[i].w * a.self_src[(int64_t)q * a.n + o];
-        double r = a.a_op * v + extra + (q == 0 ? a.add0 : (q == 1 ? a.add1 : a.add2));
-        if (a.rank1_nrm) r += rank1 * a.rank1_nrm[(int64_t)q * a.n + o];
-        if (a.xin) r += a.a_id * a.xin[(int64_t)q * a.n + o];
-        a.out[(int64_t)q * a.n + o] = r;
     }
+    double v = a.scale * s;
+    if (a.self_src) v += a.self_coef * a.pos64[i].w * a.self_src[(int64_t)q * a.n + o];
+    double r = a.a_op * v + extra + (q == 0 ? a.add0 : (q == 1 ? a.add1 : a.add2));
+    if (a.rank1_nrm) r += rank1 * a.rank1_nrm[(int64_t)q * a.n + o];
+    if (a.xin) r += a.a_id * a.xin[(int64_t)q * a.n + o];
+    a.out[(int64_t)q * a.n + o] = r;
 }
 
-template <typename R, int OP>
-cudaError_t launch_pair(dim3 grid, int tpb, const KArgs<R> &ka, cudaStream_t s) {
-    if (sizeof(R) == 4) {
-        pair_kernel<R, OP, kTPB32, kTPT32><<<grid, kTPB32, 0, s>>>(ka);
-    } else {
-        pair_kernel<R, OP, kTPB64, kTPT64><<<grid, kTPB64, 0, s>>>(ka);
-    }
-    (void)tpb;
+template <int OP>
+cudaError_t launch64(dim3 grid, const KArgs<double> &ka, cudaStream_t s) {
+    pair_kernel<double, OP, kTPB64, kTPT64><<<grid, kTPB64, 0, s>>>(ka);
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_pair_op(int op, dim3 grid, const KArgs<R> &ka, cudaStream_t s) {
+cudaError_t launch_pair_op64(int op, dim3 grid, const KArgs<double> &ka, cudaStream_t s) {
     switch (op) {
-        case OP_LSL: return launch_pair<R, OP_LSL>(grid, 0, ka, s);
-        case OP_LDL: return launch_pair<R, OP_LDL>(grid, 0, ka, s);
-        case OP_SSL: return launch_pair<R, OP_SSL>(grid, 0, ka, s);
-        case OP_SDL: return launch_pair<R, OP_SDL>(grid, 0, ka, s);
-        case OP_SSLDL: return launch_pair<R, OP_SSLDL>(grid, 0, ka, s);
-        default: return launch_pair<R, OP_LSLDL>(grid, 0, ka, s);
+        case OP_LSL: return launch64<OP_LSL>(grid, ka, s);
+        case OP_LDL: return launch64<OP_LDL>(grid, ka, s);
+        case OP_SSL: return launch64<OP_SSL>(grid, ka, s);
+        case OP_SDL: return launch64<OP_SDL>(grid, ka, s);
+        case OP_SSLDL: return launch64<OP_SSLDL>(grid, ka, s);
+        default: return launch64<OP_LSLDL>(grid, ka, s);
+    }
+}
+
+template <int OP>
+cudaError_t launch32(dim3 grid, const K32Args &ka, cudaStream_t s) {
+    pair32_kernel<OP><<<grid, kTPB32, 0, s>>>(ka);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_op32(int op, dim3 grid, const K32Args &ka, cudaStream_t s) {
+    switch (op) {
+        case OP_LSL: return launch32<OP_LSL>(grid, ka, s);
+        case OP_LDL: return launch32<OP_LDL>(grid, ka, s);
+        case OP_SSL: return launch32<OP_SSL>(grid, ka, s);
+        case OP_SDL: return launch32<OP_SDL>(grid, ka, s);
+        case OP_SSLDL: return launch32<OP_SSLDL>(grid, ka, s);
+        default: return launch32<OP_LSLDL>(grid, ka, s);
     }
 }
 
@@ -451,12 +794,144 @@ Consts<R> make_consts(double delta, double rho_far) {
     return c;
 }
 
+// ------------------------------------------------------------ batched pack/epilogue
+struct BPackArgs {
+    const int32_t *perm;
+    int64_t n_total, n_pad;       // caller points, padded layout size
+    int op;
+    const double *d0, *d1;        // [nrhs][c][n_total]
+    int nc0, nc1;                 // components of d0 and d1
+    const d4 *pos64, *wn64;
+    double s0, s1;
+    void *out0, *out1;            // records [nrhs][n_pad]
+    double *wdot_part;            // [nrhs][pack blocks]: w (d0 . n) (vector ops) or w d0 (scalar)
+    int want_wdot;
+};
+
+template <typename V4, typename R>
+__global__ void bpack_kernel(const BPackArgs a) {
+    __shared__ double red[256];
+    const int r = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double *d0 = a.d0 + (int64_t)r * a.nc0 * a.n_total;
+    const double *d1 = a.d1 ? a.d1 + (int64_t)r * a.nc1 * a.n_total : nullptr;
+    const int64_t n = a.n_total;
+    double wd = 0.0;
+    if (i < a.n_pad) {
+        const int32_t o = a.perm[i];
+        V4 r0 = {R(0), R(0), R(0), R(0)}, r1 = {R(0), R(0), R(0), R(0)};
+        if (o >= 0) {
+            const double w = a.pos64[i].w;
+            switch (a.op) {
+                case OP_LSL: r0.x = R(a.s0 * w * d0[o]); break;
+                case OP_LDL: r0.x = R(a.s0 * d0[o]); wd = w * d0[o]; break;
+                case OP_SSL:
+                    r0.x = R(a.s0 * w * d0[o]); r0.y = R(a.s0 * w * d0[n + o]); r0.z = R(a.s0 * w * d0[2 * n + o]);
+                    break;
+                case OP_SDL:
+                case OP_SSLDL:
+                    r0.x = R(a.s0 * d0[o]); r0.y = R(a.s0 * d0[n + o]); r0.z = R(a.s0 * d0[2 * n + o]);
+                    wd = a.wn64[i].x * d0[o] + a.wn64[i].y * d0[n + o] + a.wn64[i].z * d0[2 * n + o];
+                    if (a.op == OP_SSLDL) {
+                        r1.x = R(a.s1 * w * d1[o]); r1.y = R(a.s1 * w * d1[n + o]); r1.z = R(a.s1 * w * d1[2 * n + o]);
+                    }
+                    break;
+                default:  // OP_LSLDL
+                    r0.x = R(a.s0 * d0[o]);
+                    r0.y = R(a.s1 * w * d1[o]);
+                    wd = w * d0[o];
+                    break;
+            }
+        }
+        reinterpret_cast<V4 *>(a.out0)[(int64_t)r * a.n_pad + i] = r0;
+        if (a.out1) reinterpret_cast<V4 *>(a.out1)[(int64_t)r * a.n_pad + i] = r1;
+    }
+    if (a.want_wdot) {
+        red[threadIdx.x] = wd;
+        __syncthreads();
+        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.wdot_part[(int64_t)r * gridDim.x + blockIdx.x] = red[0];
+    }
+}
+
+// per (right-hand side, surface) sum of the pack blocks of that surface
+__global__ void bwdot_kernel(const double *part, int nblocks, const BSurf *surfs, int nsurf, int nrhs,
+                             const double *wsum, double *out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nsurf * nrhs) return;
+    const int r = g / nsurf, sidx = g % nsurf;
+    const int64_t b0 = surfs[sidx].poff / 256, b1 = (surfs[sidx].poff + surfs[sidx].n_pad) / 256;
+    double acc = 0.0;
+    for (int64_t b = b0; b < b1; ++b) acc += part[(int64_t)r * nblocks + b];
+    out[g] = acc / wsum[sidx];
+}
+
+struct BEpiArgs {
+    const int32_t *perm;
+    const int32_t *elem_surf;      // caller index -> surface
+    const BSurf *surfs;
+    int64_t n_total, n_pad;
+    int nc, nslot, part_is_float, nrhs, nsurf;
+    const void *part;
+    int64_t part_stride;           // per right-hand side
+    double scale;
+    double self_coef;              // times selfc[surface]
+    const double *selfc;
+    const double *self_src;        // [nrhs][nc][n_total]
+    const d4 *pos64;
+    const double *xin;
+    double a_id, a_op;
+    double add[kMaxRhs][3];
+    const double *rank1;           // [nrhs][nsurf] coefficient, or NULL
+    const double *rank1_nrm;       // [3][n_total] (vector ops) or NULL (scalar: add to every entry)
+    double *out;
+};
+
+__global__ void bepilogue_kernel(const BEpiArgs a) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per_rhs = a.n_pad * a.nc;
+    if (g >= per_rhs * a.nrhs) return;
+    const int r = (int)(g / per_rhs);
+    const int64_t rem = g - (int64_t)r * per_rhs;
+    const int q = (int)(rem / a.n_pad);
+    const int64_t i = rem - (int64_t)q * a.n_pad;
+    const int32_t o = a.perm[i];
+    if (o < 0) return;
+    const int sidx = a.elem_surf[o];
+    const BSurf sf = a.surfs[sidx];
+    const int64_t li = i - sf.poff;
+    double s = 0.0;
+    for (int64_t sp = 0; sp < sf.nsplit; ++sp) {
+        const int64_t base = (int64_t)r * a.part_stride + (int64_t)a.nc * a.nslot * sf.pbase +
+                             ((sp * a.nc + q) * a.nslot) * sf.n_pad + li;
+        if (a.part_is_float) {
+            const float *pf = reinterpret_cast<const float *>(a.part);
+            s += (double)pf[base];
+            if (a.nslot == 2) s += (double)pf[base + sf.n_pad];
+        } else {
+            s += reinterpret_cast<const double *>(a.part)[base];
+        }
+    }
+    const int64_t oi = ((int64_t)r * a.nc + q) * a.n_total + o;
+    double v = a.scale * s;
+    if (a.self_src) v += a.self_coef * a.selfc[sidx] * a.pos64[i].w * a.self_src[oi];
+    double res = a.a_op * v + a.add[r][q];
+    if (a.rank1) {
+        const double c1 = a.rank1[r * a.nsurf + sidx];
+        res += a.rank1_nrm ? c1 * a.rank1_nrm[(int64_t)q * a.n_total + o] : c1;
+    }
+    if (a.xin) res += a.a_id * a.xin[oi];
+    a.out[oi] = res;
+}
+
 }  // namespace
 
 int pair_occupancy(ssd_ctx *ctx) {
     int o32 = 0, o64 = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &o32, pair_kernel<float, OP_SSLDL, kTPB32, kTPT32>, kTPB32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, pair32_kernel<OP_SSLDL>, kTPB32, 0);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, pair_kernel<double, OP_SSLDL, kTPB64, kTPT64>,
                                                           kTPB64, 0);
@@ -474,9 +949,11 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const int tspan = f32 ? kTPB32 * kTPT32 : kTPB64 * kTPT64;
     const int64_t ntiles_t = n_pad / tspan;
     const int64_t ntiles_s = n_pad / kTile;
-    // splits: enough CTAs for about two waves of resident CTAs
+    // splits: enough CTAs for several waves of resident CTAs, so that the
+    // uneven cost of near and far target tiles evens out (FP32C: tuned on the
+    // h = 1/32 sphere, where it reaches one 128-source tile per CTA)
     const int occ = f32 ? ctx->occ32 : ctx->occ64;
-    int64_t want = (int64_t)ctx->num_sms * occ * 2;
+    int64_t want = (int64_t)ctx->num_sms * occ * (f32 ? ctx->waves32 : 2);
     int64_t nsplit = (want + ntiles_t - 1) / ntiles_t;
     if (nsplit < 1) nsplit = 1;
     if (nsplit > ntiles_s) nsplit = ntiles_s;
@@ -539,14 +1016,15 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     dim3 grid((unsigned)ntiles_t, (unsigned)nsplit);
     cudaError_t e;
     if (f32) {
-        KArgs<float> ka;
-        ka.pos = L.pos32; ka.wn = L.wn32;
+        K32Args ka;
+        ka.pos = L.pos32; ka.wn = L.wn32; ka.cbox = L.cbox;
         ka.d0 = reinterpret_cast<const float4 *>(base + o_d0);
         ka.d1 = two_rec ? reinterpret_cast<const float4 *>(base + o_d1) : ka.d0;
-        ka.n_pad = n_pad; ka.chunk = chunk;
+        ka.n = n; ka.n_pad = n_pad; ka.chunk = chunk;
         ka.c = make_consts<float>(pc.delta, kRhoFar32);
         ka.part = reinterpret_cast<float *>(base + o_part);
-        e = launch_pair_op<float>(op, grid, ka, s);
+        ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+        e = launch_pair_op32(op, grid, ka, s);
     } else {
         KArgs<double> ka;
         ka.pos = L.pos64; ka.wn = L.wn64;
@@ -555,7 +1033,8 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.n_pad = n_pad; ka.chunk = chunk;
         ka.c = make_consts<double>(pc.delta, kRhoFar64);
         ka.part = reinterpret_cast<double *>(base + o_part);
-        e = launch_pair_op<double>(op, grid, ka, s);
+        ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+        e = launch_pair_op64(op, grid, ka, s);
     }
     ctx->launches++;
     if (e != cudaSuccess) return cuda_check(ctx, e, "pair kernel launch");
@@ -571,9 +1050,200 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     ea.nwdot = pack_blocks; ea.wdot_scale = rank1 ? 1.0 / L.wsum : 0.0;
     ea.rank1_nrm = pc.rank1_nrm;
     ea.out = pc.out;
-    epilogue_kernel<<<(unsigned)((n_pad + 255) / 256), 256, 0, s>>>(ea);
+    epilogue_kernel<<<(unsigned)((n_pad * nc + 127) / 128), 128, 0, s>>>(ea);
     ctx->launches++;
     return launch_check(ctx, "epilogue kernel");
 }
 
+
+int pair_batch_items(ssd_ctx *ctx, BatchLayout *B, cudaStream_t s) {
+    const int ns = B->nsurf;
+    for (int pr = 0; pr < 2; ++pr) {   // 0: FP32C, 1: FP64
+        const int span = pr == 0 ? kTPB32 * kTPT32 : kTPB64 * kTPT64;
+        const int occ = pr == 0 ? ctx->occ32 : ctx->occ64;
+        const int64_t want = (int64_t)ctx->num_sms * occ * (pr == 0 ? ctx->waves32 : 2);
+        // source chunk (multiple of kTile) common to all surfaces: about `want` items
+        int64_t pairs_tiles = 0;
+        for (int k = 0; k < ns; ++k) pairs_tiles += (B->n_pad[k] / span) * (B->n_pad[k] / kTile);
+        int64_t chunk_tiles = pairs_tiles / want;
+        if (chunk_tiles < 1) chunk_tiles = 1;
+        std::vector<BItem> items;
+        std::vector<BSurf> surfs(ns);
+        int64_t pb = 0;
+        for (int k = 0; k < ns; ++k) {
+            const int64_t nts = B->n_pad[k] / kTile;
+            const int64_t ct = chunk_tiles < nts ? chunk_tiles : nts;
+            const int64_t nsplit = (nts + ct - 1) / ct;
+            surfs[k] = BSurf{B->poff[k], B->n_pad[k], B->n[k], pb, nsplit, 0, 0, 0};
+            for (int64_t t = 0; t < B->n_pad[k] / span; ++t)
+                for (int64_t sp = 0; sp < nsplit; ++sp) {
+                    BItem it;
+                    it.tbase = (int32_t)(B->poff[k] + t * span);
+                    it.s_beg = (int32_t)(B->poff[k] + sp * ct * kTile);
+                    int64_t e = B->poff[k] + (sp + 1) * ct * kTile;
+                    if (e > B->poff[k] + B->n_pad[k]) e = B->poff[k] + B->n_pad[k];
+                    it.s_end = (int32_t)e;
+                    it.surf = k;
+                    it.split = (int32_t)sp;
+                    it.pad0 = it.pad1 = it.pad2 = 0;
+                    items.push_back(it);
+                }
+            pb += nsplit * B->n_pad[k];
+        }
+        if (items.size() > 0x7fffffff) return set_error(ctx, SSD_EINVAL, "too many work items");
+        const size_t csz = pr == 0 ? sizeof(Consts<float>) : sizeof(Consts<double>);
+        size_t off = 0;
+        auto carve = [&](size_t bb) { size_t o = off; off += (bb + 255) & ~size_t(255); return o; };
+        const size_t o_it = carve(sizeof(BItem) * items.size()), o_sf = carve(sizeof(BSurf) * ns),
+                     o_c = carve(csz * ns);
+        void *blk = nullptr;
+        SSD_TRY(dev_alloc(ctx, off, &blk));
+        char *bp = static_cast<char *>(blk);
+        B->items[pr] = blk;
+        B->surfs[pr] = bp + o_sf;
+        B->consts[pr] = bp + o_c;
+        B->nitems[pr] = (int64_t)items.size();
+        B->ptotal[pr] = pb;
+        std::vector<char> cbuf(csz * ns);
+        for (int k = 0; k < ns; ++k) {
+            if (pr == 0) {
+                const Consts<float> c = make_consts<float>(B->delta[k], kRhoFar32);
+                memcpy(cbuf.data() + k * csz, &c, csz);
+            } else {
+                const Consts<double> c = make_consts<double>(B->delta[k], kRhoFar64);
+                memcpy(cbuf.data() + k * csz, &c, csz);
+            }
+        }
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(bp + o_it, items.data(), sizeof(BItem) * items.size(),
+                                                cudaMemcpyHostToDevice, s), "items copy"));
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(bp + o_sf, surfs.data(), sizeof(BSurf) * ns,
+                                                cudaMemcpyHostToDevice, s), "surfs copy"));
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(bp + o_c, cbuf.data(), csz * ns, cudaMemcpyHostToDevice, s),
+                           "consts copy"));
+        // the host vectors go out of scope: wait for the copies
+        SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "items sync"));
+    }
+    return SSD_OK;
+}
+
+int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cudaStream_t s) {
+    const PairCall &pc = bc.pc;
+    const int op = pc.op;
+    const int nc = op_components(op);
+    const bool f32 = (pc.prec == SSD_FP32C);
+    const int pr = f32 ? 0 : 1;
+    const int nrhs = bc.nrhs;
+    const int64_t n = B.n_total, n_pad = B.n_pad_total;
+    const int nslot = f32 ? 2 : 1;
+    const size_t rec = f32 ? sizeof(float4) : sizeof(d4);
+    const size_t rsz = f32 ? sizeof(float) : sizeof(double);
+    const bool two_rec = (op == OP_SSLDL);
+    const int pack_blocks = (int)((n_pad + 255) / 256);
+    const int64_t part_stride = (int64_t)nc * nslot * B.ptotal[pr];
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_d0 = carve(rec * n_pad * nrhs);
+    const size_t o_d1 = two_rec ? carve(rec * n_pad * nrhs) : 0;
+    const size_t o_part = carve(rsz * part_stride * nrhs);
+    const size_t o_wdot = carve(sizeof(double) * pack_blocks * nrhs);
+    const size_t o_r1 = carve(sizeof(double) * B.nsurf * nrhs);
+    void *ws = nullptr;
+    SSD_TRY(dev_alloc(ctx, off, &ws));
+    struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } release{ctx, ws};
+    char *base = static_cast<char *>(ws);
+
+    double scale = 1.0, s0 = 1.0, s1 = 1.0, self_coef = 0.0;
+    const double *self_src = nullptr;
+    switch (op) {
+        case OP_LSL: scale = -1.0 / (4.0 * kPi); self_coef = scale; self_src = pc.dens0; break;
+        case OP_LDL: scale = -1.0 / (4.0 * kPi); break;
+        case OP_SSL: scale = 1.0 / (8.0 * kPi * pc.mu); self_coef = scale; self_src = pc.dens0; break;
+        case OP_SDL: scale = 6.0 / (8.0 * kPi); break;
+        case OP_SSLDL:
+            s0 = pc.beta * 6.0 / (8.0 * kPi);
+            s1 = pc.alpha / (8.0 * kPi * pc.mu);
+            self_coef = s1; self_src = pc.dens1;
+            break;
+        default:
+            scale = -1.0 / (4.0 * kPi);
+            s0 = pc.beta; s1 = pc.alpha;
+            self_coef = scale * pc.alpha; self_src = pc.dens1;
+            break;
+    }
+    const bool rank1 = pc.rank1_weight_mean || pc.rank1_nrm != nullptr;
+    BPackArgs pa;
+    pa.perm = B.L.perm; pa.n_total = n; pa.n_pad = n_pad; pa.op = op;
+    pa.d0 = pc.dens0; pa.d1 = pc.dens1;
+    pa.nc0 = (op == OP_LSL || op == OP_LDL || op == OP_LSLDL) ? 1 : 3;
+    pa.nc1 = (op == OP_LSLDL) ? 1 : 3;
+    pa.pos64 = B.L.pos64; pa.wn64 = B.L.wn64; pa.s0 = s0; pa.s1 = s1;
+    pa.out0 = base + o_d0; pa.out1 = two_rec ? base + o_d1 : nullptr;
+    pa.wdot_part = reinterpret_cast<double *>(base + o_wdot);
+    pa.want_wdot = rank1 ? 1 : 0;
+    const dim3 pg((unsigned)pack_blocks, (unsigned)nrhs);
+    if (f32) bpack_kernel<float4, float><<<pg, 256, 0, s>>>(pa);
+    else bpack_kernel<d4, double><<<pg, 256, 0, s>>>(pa);
+    ctx->launches++;
+    SSD_TRY(launch_check(ctx, "batched pack"));
+    if (rank1) {
+        bwdot_kernel<<<(B.nsurf * nrhs + 127) / 128, 128, 0, s>>>(
+            reinterpret_cast<const double *>(base + o_wdot), pack_blocks,
+            reinterpret_cast<const BSurf *>(B.surfs[pr]), B.nsurf, nrhs, B.d_wsum,
+            reinterpret_cast<double *>(base + o_r1));
+        ctx->launches++;
+    }
+
+    cudaEvent_t ev = nullptr;
+    SSD_TRY(timed_begin(ctx, s, &ev));
+    const dim3 grid((unsigned)B.nitems[pr], (unsigned)nrhs);
+    cudaError_t e;
+    if (f32) {
+        K32Args ka;
+        ka.pos = B.L.pos32; ka.wn = B.L.wn32; ka.cbox = B.L.cbox;
+        ka.d0 = reinterpret_cast<const float4 *>(base + o_d0);
+        ka.d1 = two_rec ? reinterpret_cast<const float4 *>(base + o_d1) : ka.d0;
+        ka.n = n_pad; ka.n_pad = n_pad; ka.chunk = 0;
+        ka.c = make_consts<float>(1.0, kRhoFar32);
+        ka.part = reinterpret_cast<float *>(base + o_part);
+        ka.items = reinterpret_cast<const BItem *>(B.items[pr]);
+        ka.surfs = reinterpret_cast<const BSurf *>(B.surfs[pr]);
+        ka.consts = reinterpret_cast<const Consts<float> *>(B.consts[pr]);
+        ka.rec_stride = n_pad; ka.part_stride = part_stride;
+        e = launch_pair_op32(op, grid, ka, s);
+    } else {
+        KArgs<double> ka;
+        ka.pos = B.L.pos64; ka.wn = B.L.wn64;
+        ka.d0 = reinterpret_cast<const d4 *>(base + o_d0);
+        ka.d1 = two_rec ? reinterpret_cast<const d4 *>(base + o_d1) : ka.d0;
+        ka.n_pad = n_pad; ka.chunk = 0;
+        ka.c = make_consts<double>(1.0, kRhoFar64);
+        ka.part = reinterpret_cast<double *>(base + o_part);
+        ka.items = reinterpret_cast<const BItem *>(B.items[pr]);
+        ka.surfs = reinterpret_cast<const BSurf *>(B.surfs[pr]);
+        ka.consts = reinterpret_cast<const Consts<double> *>(B.consts[pr]);
+        ka.rec_stride = n_pad; ka.part_stride = part_stride;
+        e = launch_pair_op64(op, grid, ka, s);
+    }
+    ctx->launches++;
+    if (e != cudaSuccess) return cuda_check(ctx, e, "batched pair kernel launch");
+    double pairs = 0.0;
+    for (int k = 0; k < B.nsurf; ++k) pairs += (double)B.n[k] * (double)B.n[k];
+    timed_end(ctx, s, ev, kernel_class(op), pc.prec, pairs * nrhs);
+
+    BEpiArgs ea;
+    ea.perm = B.L.perm; ea.elem_surf = B.elem_surf; ea.surfs = reinterpret_cast<const BSurf *>(B.surfs[pr]);
+    ea.n_total = n; ea.n_pad = n_pad; ea.nc = nc; ea.nslot = nslot; ea.part_is_float = f32 ? 1 : 0;
+    ea.nrhs = nrhs; ea.nsurf = B.nsurf; ea.part = base + o_part; ea.part_stride = part_stride;
+    ea.scale = scale; ea.self_coef = self_coef; ea.selfc = B.d_selfc; ea.self_src = self_src;
+    ea.pos64 = B.L.pos64; ea.xin = pc.xin; ea.a_id = pc.a_id; ea.a_op = pc.a_op;
+    for (int r = 0; r < kMaxRhs; ++r)
+        for (int q = 0; q < 3; ++q) ea.add[r][q] = (r < nrhs ? bc.add[r][q] : 0.0) + (q < 3 ? 0.0 : 0.0);
+    ea.rank1 = rank1 ? reinterpret_cast<const double *>(base + o_r1) : nullptr;
+    ea.rank1_nrm = pc.rank1_nrm;
+    ea.out = pc.out;
+    const int64_t tot = n_pad * nc * nrhs;
+    bepilogue_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(ea);
+    ctx->launches++;
+    return launch_check(ctx, "batched epilogue");
+}
 }  // namespace ssd

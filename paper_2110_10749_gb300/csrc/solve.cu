@@ -16,6 +16,7 @@ constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------ vector kernels
 constexpr int kDotThreads = 256;
+constexpr int kMaxRestart = 256;
 constexpr int kDotMaxBlocks = 120;
 
 // partial[v * nbx + bx] = sum over this block's chunk of V[v] . w
@@ -49,7 +50,7 @@ __global__ void multidot_finish_kernel(const double *partial, int nbx, int nv, d
 // w += sign * sum_v coef[v] V[v]
 __global__ void vupdate_kernel(const double *V, int64_t ldv, int nv, const double *coef, double sign, double *w,
                                int64_t n) {
-    __shared__ double c[130];
+    __shared__ double c[kMaxRestart + 2];
     for (int v = threadIdx.x; v < nv; v += blockDim.x) c[v] = sign * coef[v];
     __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -377,8 +378,8 @@ int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
     if (!kr) return set_error(ctx, SSD_EINVAL, "krylov settings are NULL");
     if (!(kr->tol > 0.0) || !isfinite(kr->tol)) return set_error(ctx, SSD_EINVAL, "tolerance must be positive");
     if (kr->maxit < 1) return set_error(ctx, SSD_EINVAL, "maxit must be >= 1");
-    if (!kr->use_sa && (kr->restart < 1 || kr->restart > 128))
-        return set_error(ctx, SSD_EINVAL, "restart must be in 1..128");
+    if (!kr->use_sa && (kr->restart < 1 || kr->restart > kMaxRestart))
+        return set_error(ctx, SSD_EINVAL, "restart must be in 1..256");
     if (kr->prec != SSD_FP64 && kr->prec != SSD_FP32C) return set_error(ctx, SSD_EINVAL, "unknown precision");
     return SSD_OK;
 }

@@ -1,0 +1,123 @@
+"""Batched launches over several surfaces (uneven point counts, one smoothing
+radius each) and several right-hand sides, against the oracle surface by
+surface and against the single-surface device path."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as A
+from oracle import quadrature as Q
+from oracle import solvers as S
+
+pytestmark = pytest.mark.gpu
+
+SURFS = [((1.0, 1.0, 1.0), 1 / 8), ((1.0, 0.6, 0.4), 1 / 12), ((1.0, 0.8, 0.6), 1 / 10), ((0.8, 0.8, 0.8), 1 / 12)]
+
+
+@pytest.fixture(scope="module")
+def batch(gpu_ctx):
+    import paper_2110_10749_gb300 as ssd
+    pts = [Q.ellipsoid_points(abc, h) for abc, h in SURFS]
+    deltas = [3 * h for _, h in SURFS]
+    B = ssd.Batch.from_numpy(pts, deltas).prepare(gpu_ctx)
+    yield pts, deltas, B
+    B.release()
+
+
+def test_batched_operators_match_oracle(gpu_ctx, batch):
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    pts, deltas, B = batch
+    offs = np.concatenate([[0], np.cumsum([p["w"].size for p in pts])])
+    n = offs[-1]
+    rng = np.random.default_rng(21)
+    nrhs = 3
+    g = rng.normal(size=(nrhs, 1, n))
+    v = rng.normal(size=(nrhs, 3, n))
+    v2 = rng.normal(size=(nrhs, 3, n))
+    tg, tv, tv2 = (torch.as_tensor(a, device="cuda") for a in (g, v, v2))
+    for prec, tol in ((ssd.FP64, 1e-12), (ssd.FP32C, 1e-5)):
+        outs = {
+            "LSL": ssd.batch_apply(gpu_ctx, B, ssd.OP_LAPLACE_SL, tg, prec=prec),
+            "LDL": ssd.batch_apply(gpu_ctx, B, ssd.OP_LAPLACE_DL, tg, prec=prec),
+            "SSL": ssd.batch_apply(gpu_ctx, B, ssd.OP_STOKES_SL, tv, mu=1.3, prec=prec),
+            "SDL": ssd.batch_apply(gpu_ctx, B, ssd.OP_STOKES_DL, tv, prec=prec),
+            "SSLDL": ssd.batch_apply(gpu_ctx, B, ssd.OP_STOKES_SLDL, tv, tv2, mu=1.3, alpha=0.7, beta=-1.1,
+                                     prec=prec),
+        }
+        outs = {k: o.cpu().numpy() for k, o in outs.items()}
+        for r in range(nrhs):
+            for s, p in enumerate(pts):
+                sl = slice(offs[s], offs[s + 1])
+                d = deltas[s]
+                ref = {"LSL": oracle.laplace_sl(p, d, g[r, 0, sl]), "LDL": oracle.laplace_dl(p, d, g[r, 0, sl]),
+                       "SSL": oracle.stokes_sl(p, d, 1.3, v[r][:, sl]), "SDL": oracle.stokes_dl(p, d, v[r][:, sl]),
+                       "SSLDL": 0.7 * oracle.stokes_sl(p, d, 1.3, v2[r][:, sl]) - 1.1 * oracle.stokes_dl(p, d, v[r][:, sl])}
+                for k, rv in ref.items():
+                    got = outs[k][r][..., sl].reshape(rv.shape)
+                    rel = np.linalg.norm(got - rv) / np.linalg.norm(rv)
+                    assert rel < tol, (prec, k, r, s, rel)
+
+
+def test_batched_ddm_matches_single_surface_solves(gpu_ctx, batch):
+    import paper_2110_10749_gb300 as ssd
+    pts, deltas, B = batch
+    offs = np.concatenate([[0], np.cumsum([p["w"].size for p in pts])])
+    uinf = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.3, -0.2, 0.5]])
+    kappa, gamma = 1e-2, 1.0
+    for prec, tol in ((ssd.FP64, 1e-8), (ssd.FP32C, 1e-5)):
+        inner = ssd.krylov(1e-10 if prec == ssd.FP64 else 1e-9, 200, 200, False, prec, deflate=True)
+        prm = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=gamma, theta=0.5 * kappa,
+                             tol_outer=1e-9 if prec == ssd.FP64 else 1e-8, maxit_outer=100, outer_gmres=True,
+                             traction_mode=ssd.TRACTION_BJS, bjs_implicit=True, inner=inner)
+        rb = ssd.batch_ddm_solve(gpu_ctx, B, prm, uinf)
+        assert rb["status"] == ssd.SSD_OK
+        for r in range(uinf.shape[0]):
+            for s, p in enumerate(pts):
+                sl = slice(offs[s], offs[s + 1])
+                P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
+                prm1 = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=gamma, uinf=tuple(uinf[r]), delta=deltas[s],
+                                      theta=0.5 * kappa, tol_outer=prm.tol_outer, maxit_outer=100, outer_gmres=True,
+                                      traction_mode=ssd.TRACTION_BJS, bjs_implicit=True, inner=inner)
+                r1 = ssd.ddm_solve(gpu_ctx, P, prm1)
+                P.release()
+                for k in ("p", "u", "f"):
+                    a = rb[k][r][..., sl].cpu().numpy().reshape(r1[k].shape)
+                    b = r1[k].cpu().numpy()
+                    assert np.linalg.norm(a - b) / np.linalg.norm(b) < tol, (prec, k, r, s)
+                # drag components that vanish by symmetry differ at the solve tolerance
+                assert np.allclose(rb["drag"][r, s], r1["drag"], rtol=tol, atol=1e-7)
+
+
+def test_batched_benchmark_mode_against_oracle(gpu_ctx):
+    # two spheres of different h in one batch, porous-sphere benchmark traction
+    import paper_2110_10749_gb300 as ssd
+    hs = [1 / 8, 1 / 10]
+    pts = [Q.sphere_points(1.0, h) for h in hs]
+    B = ssd.Batch.from_numpy(pts, [3 * h for h in hs]).prepare(gpu_ctx)
+    inner = ssd.krylov(1e-10, 200, 200, False, ssd.FP64)
+    prm = ssd.ddm_params(mu=1.0, kappa=1.0, theta=0.75, tol_outer=1e-9, maxit_outer=50, outer_gmres=True,
+                         traction_mode=ssd.TRACTION_JOSEPH_TAO, radius=1.0, inner=inner)
+    rb = ssd.batch_ddm_solve(gpu_ctx, B, prm, [[0.0, 0.0, 1.0]])
+    offs = np.concatenate([[0], np.cumsum([p["w"].size for p in pts])])
+    for s, (p, h) in enumerate(zip(pts, hs)):
+        ro = S.ddm_solve(p, 3 * h, 1.0, 1.0, 0.0, [0, 0, 1.0], 0.75, tol=1e-9, maxit=50, outer="gmres", traction="jt",
+                         inner_tol=1e-10)
+        sl = slice(offs[s], offs[s + 1])
+        assert np.abs(rb["p"][0, 0, sl].cpu().numpy() - ro["p"]).max() < 1e-7
+        assert np.abs(rb["u"][0][:, sl].cpu().numpy() - ro["u"]).max() < 1e-7
+        D = A.jt_drag(1.0, 1.0, 1.0, 1.0)
+        assert abs(rb["drag"][0, s, 2] - ro["drag"][2]) < 1e-7 and abs(rb["drag"][0, s, 2] - D) / D < 1e-2
+    B.release()
+
+
+def test_batch_argument_errors(gpu_ctx, batch):
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    pts, deltas, B = batch
+    g = torch.zeros((17, 1, B.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(ssd.SsdError):
+        ssd.batch_apply(gpu_ctx, B, ssd.OP_LAPLACE_SL, g)   # nrhs > 16
+    prm = ssd.ddm_params(kappa=1.0, gamma=1.0, outer_gmres=True, traction_mode=ssd.TRACTION_BJS, bjs_implicit=False)
+    with pytest.raises(ssd.SsdError):
+        ssd.batch_ddm_solve(gpu_ctx, B, prm, [[0, 0, 1.0]])  # lagged BJS is not batched
