@@ -161,6 +161,22 @@ int ssd_stokes_SL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu,
  * T^delta_abc = -6 yhat_a yhat_b yhat_c s4/r^5.  D^S = K + I/2 (eq. K_subtr).  u, out [3][n]. */
 int ssd_stokes_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u,
                   double *out, int prec, ssd_stream stream);
+/* The Stokes double layer of ssd_stokes_DL in FP32C, without any device
+ * allocation.  The paper has no counterpart: this call is for callers that
+ * cannot call cudaMalloc at this point, for example code whose device memory
+ * is reserved up front by another allocator (so a new allocation can fail),
+ * or code that must not trigger the device-wide synchronisation a cudaFree
+ * implies.  Inputs and output are the caller's (pts->layout is ignored; the
+ * points are used in caller order).  Scratch: one file-scope device array of
+ * 16 MiB, held on every device that loads the library until the process
+ * exits.  Limit: n rounded up to a multiple of 512 must not exceed 32768
+ * (larger sets give SSD_EINVAL before any work).  The first call on a device
+ * looks up the array's device address with that device current; make it
+ * before any stream capture.  All calls share the array: calls whose work can
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
+int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u,
+                          double *out, ssd_stream stream);
 /* One pass sharing r, erf and exp between both layers:
  * out = alpha (M f) + beta (D^S u)   [Stokes],   out = alpha (L g) + beta (D^L p)   [Laplace].
  * Used for the right-hand sides and residuals b - A x of the local solves. */

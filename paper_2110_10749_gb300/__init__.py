@@ -36,6 +36,7 @@ EXPORTS = [
     "ssd_stokes_SLDL", "ssd_laplace_SLDL",
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
+    "ssd_stokes_DL_noalloc",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 
@@ -131,6 +132,7 @@ def lib():
                           C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
         "ssd_ddm_solve_host": [P, i64, P, P, P, C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
                                C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
+        "ssd_stokes_DL_noalloc": [P, C.POINTER(CPoints), d, P, P, P],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
         "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
@@ -293,6 +295,14 @@ def stokes_DL(ctx, pts, delta, u, prec=FP64, out=None):
     out = _out_like(u, out)
     ctx.check(lib().ssd_stokes_DL(ctx.h, C.byref(pts.c), float(delta), _ptr(u), _ptr(out), prec, _stream()),
               "ssd_stokes_DL")
+    return out
+
+
+def stokes_DL_noalloc(ctx, pts, delta, u, out=None):
+    """Stokes double layer in FP32C without device allocation (see include/ssd.h)."""
+    out = _out_like(u, out)
+    ctx.check(lib().ssd_stokes_DL_noalloc(ctx.h, C.byref(pts.c), float(delta), _ptr(u), _ptr(out), _stream()),
+              "ssd_stokes_DL_noalloc")
     return out
 
 

@@ -20,6 +20,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "internal.h"
 #include "erfcx_coef.h"
 #include "series_coef.h"
@@ -1247,3 +1249,161 @@ int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cu
     return launch_check(ctx, "batched epilogue");
 }
 }  // namespace ssd
+
+// ===================================================================== no-alloc
+// Stokes double layer (FP32C) that allocates no device memory: the unsorted
+// point layout, the packed density and the per-split partial sums all live in
+// one file-scope device array of fixed size, whose device address is looked
+// up once per device.  Each call rewrites every region it later reads, so no
+// state carries over between calls.  For callers that cannot call cudaMalloc
+// (see ssd_stokes_DL_noalloc in include/ssd.h).
+namespace ssd {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 32768;                  // points per call (after padding)
+constexpr int kNoAllocMaxSplit = 16;
+constexpr size_t kNoAllocBytes = 16u << 20;              // 16 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_ptr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// unsorted layout of the caller's points inside the scratch array
+__global__ void noalloc_layout_kernel(const double *xyz, const double *nrm, const double *w, int64_t n,
+                                      int64_t n_pad, Layout L) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    if (i < n) {
+        const double x = xyz[i], y = xyz[n + i], z = xyz[2 * n + i], ww = w[i];
+        const double wx = ww * nrm[i], wy = ww * nrm[n + i], wz = ww * nrm[2 * n + i];
+        L.perm[i] = (int32_t)i;
+        L.pos64[i] = d4{x, y, z, ww};
+        L.wn64[i] = d4{wx, wy, wz, 0.0};
+        L.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)ww);
+        L.wn32[i] = make_float4((float)wx, (float)wy, (float)wz, 0.f);
+    } else {
+        const double far = 1.0e4;
+        L.perm[i] = -1;
+        L.pos64[i] = d4{far, far, far, 0.0};
+        L.wn64[i] = d4{0.0, 0.0, 0.0, 0.0};
+        L.pos32[i] = make_float4((float)far, (float)far, (float)far, 0.f);
+        L.wn32[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void noalloc_chunk_box_kernel(Layout L) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L.n_pad / kChunk) return;
+    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+    bool any = false;
+    for (int k = 0; k < kChunk; ++k) {
+        const int64_t i = c * kChunk + k;
+        if (i >= L.n) break;
+        const float4 p = L.pos32[i];
+        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+        any = true;
+    }
+    if (!any) {
+        const float4 p = L.pos32[c * kChunk];
+        lo[0] = hi[0] = p.x; lo[1] = hi[1] = p.y; lo[2] = hi[2] = p.z;
+    }
+    L.cbox[2 * c] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    L.cbox[2 * c + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+}
+
+// Device address of the scratch array for the current device; looked up
+// once per device (host code must not pass the symbol itself to a kernel).
+int noalloc_scratch(ssd_ctx *ctx, char **out) {
+    int dev = 0;
+    SSD_TRY(cuda_check(ctx, cudaGetDevice(&dev), "cudaGetDevice"));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(ctx, SSD_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<char *>(g_noalloc_ptr[dev]);
+    return SSD_OK;
+}
+
+}  // namespace
+}  // namespace ssd
+
+extern "C" int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u,
+                                     double *out, ssd_stream stream) {
+    using namespace ssd;
+    if (!ctx) return SSD_EINVAL;
+    if (!pts || pts->n <= 0 || !pts->xyz || !pts->nrm || !pts->w)
+        return set_error(ctx, SSD_EINVAL, "bad point set");
+    if (!(delta > 0.0) || !isfinite(delta)) return set_error(ctx, SSD_EINVAL, "delta must be positive");
+    if (!u || !out) return set_error(ctx, SSD_EINVAL, "NULL density or output");
+    const int64_t n = pts->n;
+    const int64_t n_pad = ((n + kRowAlign - 1) / kRowAlign) * kRowAlign;
+    if (n_pad > kNoAllocMaxN)
+        return set_error(ctx, SSD_EINVAL, "ssd_stokes_DL_noalloc: more than 32768 points (after padding to 512)");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = nullptr;
+    SSD_TRY(noalloc_scratch(ctx, &base));
+
+    // carve the scratch array
+    size_t off = 0;
+    auto carve = [&](size_t b) { size_t o = off; off += (b + 255) & ~size_t(255); return o; };
+    Layout L;
+    L.n = n;
+    L.n_pad = n_pad;
+    L.perm = reinterpret_cast<int32_t *>(base + carve(sizeof(int32_t) * n_pad));
+    L.pos32 = reinterpret_cast<float4 *>(base + carve(sizeof(float4) * n_pad));
+    L.wn32 = reinterpret_cast<float4 *>(base + carve(sizeof(float4) * n_pad));
+    L.pos64 = reinterpret_cast<d4 *>(base + carve(sizeof(d4) * n_pad));
+    L.wn64 = reinterpret_cast<d4 *>(base + carve(sizeof(d4) * n_pad));
+    L.cbox = reinterpret_cast<float4 *>(base + carve(sizeof(float4) * 2 * (n_pad / kChunk)));
+    float4 *d0 = reinterpret_cast<float4 *>(base + carve(sizeof(float4) * n_pad));
+    const int64_t ntiles_t = n_pad / (kTPB32 * kTPT32);
+    const int64_t ntiles_s = n_pad / kTile;
+    int64_t nsplit = ((int64_t)ctx->num_sms * ctx->occ32 * ctx->waves32 + ntiles_t - 1) / ntiles_t;
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > kNoAllocMaxSplit) nsplit = kNoAllocMaxSplit;
+    if (nsplit > ntiles_s) nsplit = ntiles_s;
+    const int64_t chunk_tiles = (ntiles_s + nsplit - 1) / nsplit;
+    nsplit = (ntiles_s + chunk_tiles - 1) / chunk_tiles;
+    float *part = reinterpret_cast<float *>(base + carve(sizeof(float) * 2 * 3 * nsplit * n_pad));
+    if (off > kNoAllocBytes) return set_error(ctx, SSD_EINVAL, "no-alloc scratch too small");
+
+    const unsigned nb = (unsigned)((n_pad + 255) / 256);
+    noalloc_layout_kernel<<<nb, 256, 0, s>>>(pts->xyz, pts->nrm, pts->w, n, n_pad, L);
+    noalloc_chunk_box_kernel<<<(unsigned)((n_pad / kChunk + 127) / 128), 128, 0, s>>>(L);
+    PackArgs pa;
+    pa.perm = L.perm; pa.n = n; pa.n_pad = n_pad; pa.op = OP_SDL;
+    pa.d0 = u; pa.d1 = nullptr; pa.pos64 = L.pos64; pa.wn64 = L.wn64; pa.s0 = 1.0; pa.s1 = 1.0;
+    pa.out0 = d0; pa.out1 = nullptr; pa.wdot_part = nullptr;
+    pack_kernel<float4, float><<<nb, 256, 0, s>>>(pa);
+    ctx->launches += 3;
+    SSD_TRY(launch_check(ctx, "no-alloc layout"));
+
+    K32Args ka;
+    ka.pos = L.pos32; ka.wn = L.wn32; ka.cbox = L.cbox; ka.d0 = d0; ka.d1 = d0;
+    ka.n = n; ka.n_pad = n_pad; ka.chunk = chunk_tiles * kTile;
+    ka.c = make_consts<float>(delta, kRhoFar32);
+    ka.part = part;
+    ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+    pair32_kernel<OP_SDL><<<dim3((unsigned)ntiles_t, (unsigned)nsplit), kTPB32, 0, s>>>(ka);
+    ctx->launches++;
+    SSD_TRY(launch_check(ctx, "no-alloc pair kernel"));
+
+    EpiArgs ea;
+    ea.perm = L.perm; ea.n = n; ea.n_pad = n_pad; ea.nc = 3; ea.nsplit = (int)nsplit; ea.nslot = 2;
+    ea.part_is_float = 1; ea.part = part;
+    ea.scale = 6.0 / (8.0 * kPi); ea.self_coef = 0.0; ea.self_src = nullptr; ea.pos64 = L.pos64;
+    ea.xin = nullptr; ea.a_id = 0.0; ea.a_op = 1.0;
+    ea.add0 = ea.add1 = ea.add2 = 0.0; ea.add_dev = nullptr;
+    ea.wdot_part = nullptr; ea.nwdot = 0; ea.wdot_scale = 0.0; ea.rank1_nrm = nullptr;
+    ea.out = out;
+    epilogue_kernel<<<(unsigned)((n_pad * 3 + 127) / 128), 128, 0, s>>>(ea);   // one thread per point and component
+    ctx->launches++;
+    return launch_check(ctx, "no-alloc epilogue");
+}
