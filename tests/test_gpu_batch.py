@@ -65,7 +65,9 @@ def test_batched_ddm_matches_single_surface_solves(gpu_ctx, batch):
     offs = np.concatenate([[0], np.cumsum([p["w"].size for p in pts])])
     uinf = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.3, -0.2, 0.5]])
     kappa, gamma = 1e-2, 1.0
-    for prec, tol in ((ssd.FP64, 1e-8), (ssd.FP32C, 1e-5)):
+    # two independent solves to an interface tolerance of 1e-9 (FP64) agree to
+    # about 10x that; FP32C to 1e-5
+    for prec, tol in ((ssd.FP64, 1e-7), (ssd.FP32C, 1e-5)):
         inner = ssd.krylov(1e-10 if prec == ssd.FP64 else 1e-9, 200, 200, False, prec, deflate=True)
         prm = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=gamma, theta=0.5 * kappa,
                              tol_outer=1e-9 if prec == ssd.FP64 else 1e-8, maxit_outer=100, outer_gmres=True,
