@@ -73,7 +73,8 @@ const char *ssd_ctx_last_error(const ssd_ctx *ctx);
 enum ssd_kernel_class {
     SSD_K_LAPLACE_SL = 0, SSD_K_LAPLACE_DL = 1, SSD_K_STOKES_SL = 2,
     SSD_K_STOKES_DL = 3, SSD_K_STOKES_SLDL = 4, SSD_K_LAPLACE_SLDL = 5,
-    SSD_K_COUNT = 6
+    SSD_K_LAPLACE_DL_T = 6, SSD_K_STOKES_DL_T = 7,
+    SSD_K_COUNT = 8
 };
 typedef struct {
     int64_t launches;  /* pair-sum kernel launches */
@@ -187,6 +188,19 @@ int ssd_laplace_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, const do
                      const double *p, double alpha, double beta, double *out, int prec,
                      ssd_stream stream);
 
+/*
+ * Transposes of the discrete operators, for adjoint (reverse-mode) solves.
+ * With A the matrix that ssd_laplace_SL / _DL / ssd_stokes_SL / _DL apply
+ * (op = enum ssd_operator, SL or DL only), out = A^T dens:
+ *   single layers: A = S W with S symmetric, so A^T v = W S v (w at the target);
+ *   Laplace DL:  (A^T v)_i = 1/(4 pi) sum_j s2/r^3 [(yhat.w_i n_i) v_j + (yhat.w_j n_j) v_i];
+ *   Stokes DL:   (A^T v)_i = -3/(4 pi) sum_j s4/r^5 yhat [(yhat.w_i n_i)(yhat.v_j) + (yhat.w_j n_j)(yhat.v_i)],
+ * yhat = x_i - x_j (the second terms are the transposed subtraction).
+ * mu is used by the Stokes single layer only.  Asynchronous on `stream`.
+ */
+int ssd_apply_transpose(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu,
+                        const double *dens, double *out, int prec, ssd_stream stream);
+
 /* ------------------------------------------------------------ local solves */
 
 typedef struct {
@@ -281,6 +295,28 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
                        const double *w, const ssd_ddm_params *prm, double *q, double *p_D,
                        double *u_S, double *f_S, double drag[3], int *outer_its,
                        int *inner_its, double *res_hist, ssd_stream stream);
+
+/* ---------------------------------------------------------------- adjoint
+ * Derivatives of a scalar output of the Dirichlet-Neumann solve with respect
+ * to the two physical parameters of Sections 2 and 7, log(kappa) and gamma,
+ * by the discrete adjoint of the computed map (the paper reports drag against
+ * kappa and gamma in Section 7 and Tables 1-2; it computes no derivatives).
+ * Functionals, e = U_inf / |U_inf| (e = z when U_inf = 0):
+ *   SSD_FUNC_DRAG: J = e . sum_x w f           (drag along the flow, eq. drag_int)
+ *   SSD_FUNC_FLUX: J = sum_x w q (e . x)       (first moment of the interface flux)
+ * Requirements: outer_gmres = 1, inner.use_sa = 0, and in BJS mode with
+ * gamma != 0 bjs_implicit = 1 (the lagged slip has no fixed-point map in q
+ * alone).  Cost: one forward solve, one transposed interface GMRES (each
+ * matvec one transposed Stokes and one transposed Darcy solve) and, for the
+ * drag with BJS slip, one more transposed Stokes solve.
+ * Host outputs: *value = J (may be NULL), grad[0] = dJ/dlog(kappa),
+ * grad[1] = dJ/dgamma (0 in JOSEPH_TAO mode, where gamma does not enter).
+ * Returns SSD_ENOTCONV (with the values filled) when a forward or adjoint
+ * solve hit its iteration limit.  Synchronises `stream`.
+ */
+enum ssd_functional { SSD_FUNC_DRAG = 0, SSD_FUNC_FLUX = 1 };
+int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
+                     int functional, double *value, double grad[2], ssd_stream stream);
 
 /* ------------------------------------------------------------------ batches
  * Many independent surfaces (uneven point counts, one smoothing radius each)

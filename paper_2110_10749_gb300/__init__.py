@@ -25,7 +25,7 @@ SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECUDA, SSD_ENOTCONV, SSD_ENUMERIC = range(6)
 FP64, FP32C = 0, 1
 SPHERE, ELLIPSOID = 0, 1
 TRACTION_BJS, TRACTION_JOSEPH_TAO = 0, 1
-K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_SLDL = range(6)
+K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_SLDL, K_LAPLACE_DL_T, K_STOKES_DL_T = range(8)
 
 # Every entry point declared in include/ssd.h.
 EXPORTS = [
@@ -36,9 +36,10 @@ EXPORTS = [
     "ssd_stokes_SLDL", "ssd_laplace_SLDL",
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
-    "ssd_stokes_DL_noalloc",
+    "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
+FUNC_DRAG, FUNC_FLUX = 0, 1
 
 
 class SsdError(RuntimeError):
@@ -133,6 +134,8 @@ def lib():
         "ssd_ddm_solve_host": [P, i64, P, P, P, C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
                                C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
         "ssd_stokes_DL_noalloc": [P, C.POINTER(CPoints), d, P, P, P],
+        "ssd_apply_transpose": [P, C.POINTER(CPoints), i, d, d, P, P, i, P],
+        "ssd_ddm_gradient": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(d), C.POINTER(d), P],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
         "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
@@ -298,6 +301,14 @@ def stokes_DL(ctx, pts, delta, u, prec=FP64, out=None):
     return out
 
 
+def apply_transpose(ctx, pts, op, delta, dens, mu=1.0, prec=FP64, out=None):
+    """out = A^T dens for op in OP_LAPLACE_SL/DL, OP_STOKES_SL/DL (adjoint operators)."""
+    out = _out_like(dens, out)
+    ctx.check(lib().ssd_apply_transpose(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu), _ptr(dens),
+                                        _ptr(out), int(prec), _stream()), "ssd_apply_transpose")
+    return out
+
+
 def stokes_DL_noalloc(ctx, pts, delta, u, out=None):
     """Stokes double layer in FP32C without device allocation (see include/ssd.h)."""
     out = _out_like(u, out)
@@ -404,6 +415,48 @@ def ddm_solve_host(ctx, xyz, nrm, w, prm, out=None, raise_on_notconv=True):
     out["drag"] = np.array(drag[:])
     out["outer_its"] = oits.value
     return out
+
+
+def ddm_gradient(ctx, pts, prm, functional=FUNC_DRAG, raise_on_notconv=True):
+    """J and (dJ/dlog(kappa), dJ/dgamma) of the D-N solve by the discrete adjoint.
+
+    Returns (value, grad[2] as numpy, status)."""
+    val = C.c_double()
+    g = (C.c_double * 2)()
+    st = lib().ssd_ddm_gradient(ctx.h, C.byref(pts.c), C.byref(prm), int(functional), C.byref(val), g, _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_ddm_gradient")
+    return val.value, np.array(g[:]), st
+
+
+_DdmFunction = None
+
+
+def ddm_functional(ctx, pts, prm, log_kappa, gamma, functional=FUNC_DRAG):
+    """Differentiable J(log(kappa), gamma) for torch.autograd.
+
+    ``log_kappa`` and ``gamma`` are 0-d float64 tensors; the other parameters
+    come from ``prm`` (left unchanged).  The backward pass uses the gradient
+    that ssd_ddm_gradient computes together with J."""
+    global _DdmFunction
+    torch = _torch()
+    if _DdmFunction is None:
+        class DdmFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, lk, gm, c, pts_, prm_, func):
+                p2 = CDdmParams.from_buffer_copy(prm_)
+                p2.kappa = float(np.exp(float(lk)))
+                p2.gamma = float(gm)
+                value, grad, _ = ddm_gradient(c, pts_, p2, func)
+                fctx.save_for_backward(torch.tensor(grad, dtype=torch.float64, device=lk.device))
+                return torch.tensor(value, dtype=torch.float64, device=lk.device)
+
+            @staticmethod
+            def backward(fctx, gout):
+                (grad,) = fctx.saved_tensors
+                return gout * grad[0], gout * grad[1], None, None, None, None
+        _DdmFunction = DdmFunction
+    return _DdmFunction.apply(log_kappa, gamma, ctx, pts, prm, functional)
 
 
 class Batch:

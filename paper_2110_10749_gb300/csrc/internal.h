@@ -28,8 +28,11 @@ constexpr int kTPT64 = 1;           // targets per thread, FP64
 constexpr int kRowAlign = 512;      // n_pad is a multiple of this (>= every CTA target span)
 
 // Operators of the pair kernels.
-enum Op { OP_LSL = 0, OP_LDL = 1, OP_SSL = 2, OP_SDL = 3, OP_SSLDL = 4, OP_LSLDL = 5 };
-inline int op_components(int op) { return (op == OP_LSL || op == OP_LDL || op == OP_LSLDL) ? 1 : 3; }
+// OP_LDLT, OP_SDLT: transposes of the subtracted double layers (adjoints)
+enum Op { OP_LSL = 0, OP_LDL = 1, OP_SSL = 2, OP_SDL = 3, OP_SSLDL = 4, OP_LSLDL = 5, OP_LDLT = 6, OP_SDLT = 7 };
+inline int op_components(int op) {
+    return (op == OP_LSL || op == OP_LDL || op == OP_LSLDL || op == OP_LDLT) ? 1 : 3;
+}
 
 struct alignas(16) d4 { double x, y, z, w; };
 
@@ -127,6 +130,7 @@ struct PairCall {
     bool rank1_weight_mean = false;       // add (w . dens0) / sum(w) to every entry (Darcy gauge)
     const double *rank1_nrm = nullptr;    // vector ops: add n (w . (dens0 . n)) / sum(w) (Stokes
                                           // normal-mode deflation); caller-order normals [3][n]
+    bool transpose_sl = false;            // OP_LSL / OP_SSL: apply the transpose W S W^{-1}
     double *out = nullptr;
 };
 int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s);

@@ -41,6 +41,8 @@ template <> struct OpInfo<OP_SSL>   { enum { NC = 3, WN = 0, D1 = 0, SL = 1, DL 
 template <> struct OpInfo<OP_SDL>   { enum { NC = 3, WN = 1, D1 = 0, SL = 0, DL = 1 }; };
 template <> struct OpInfo<OP_SSLDL> { enum { NC = 3, WN = 1, D1 = 1, SL = 1, DL = 1 }; };
 template <> struct OpInfo<OP_LSLDL> { enum { NC = 1, WN = 1, D1 = 0, SL = 1, DL = 1 }; };
+template <> struct OpInfo<OP_LDLT>  { enum { NC = 1, WN = 1, D1 = 0, SL = 0, DL = 1 }; };
+template <> struct OpInfo<OP_SDLT>  { enum { NC = 3, WN = 1, D1 = 0, SL = 0, DL = 1 }; };
 
 // ---------------------------------------------------------------- precision
 template <typename R> struct Prec;
@@ -125,11 +127,11 @@ __device__ __forceinline__ void smooth(R r2, const Consts<R> &c, bool anyser, R 
         k1 = s1 * rinv;
         k3 = s3 * rinv3;
     }
-    if (OP == OP_LDL || OP == OP_LSLDL) {
+    if (OP == OP_LDL || OP == OP_LSLDL || OP == OP_LDLT) {
         const R s2 = er + ce * ((R(2) * t - R(3)) * third);
         k2 = s2 * rinv3;
     }
-    if (OP == OP_SDL || OP == OP_SSLDL) {
+    if (OP == OP_SDL || OP == OP_SSLDL || OP == OP_SDLT) {
         const R s4 = er - ce * ((t * (t * (R(8) * t - R(36)) + R(6)) + R(9)) * (R(1) / R(9)));
         k4 = s4 * rinv3 * rinv2;
     }
@@ -138,8 +140,8 @@ __device__ __forceinline__ void smooth(R r2, const Consts<R> &c, bool anyser, R 
             k1 = P::ser(0, t) * c.inv_d;
             k3 = P::ser(2, t) * c.inv_d3;
         }
-        if (OP == OP_LDL || OP == OP_LSLDL) k2 = P::ser(1, t) * c.inv_d3;
-        if (OP == OP_SDL || OP == OP_SSLDL) k4 = P::ser(3, t) * c.inv_d5;
+        if (OP == OP_LDL || OP == OP_LSLDL || OP == OP_LDLT) k2 = P::ser(1, t) * c.inv_d3;
+        if (OP == OP_SDL || OP == OP_SSLDL || OP == OP_SDLT) k4 = P::ser(3, t) * c.inv_d5;
     }
 }
 
@@ -149,7 +151,8 @@ __device__ __forceinline__ void smooth(R r2, const Consts<R> &c, bool anyser, R 
 template <typename R, int OP, bool NEAR>
 __device__ __forceinline__ void pair_term(const R d[3], const R r2, const R dt[3], const typename Prec<R>::V4 &sw,
                                           const typename Prec<R>::V4 &s0, const typename Prec<R>::V4 &s1,
-                                          const Consts<R> &c, bool anyser, bool self, R acc[3]) {
+                                          const Consts<R> &c, bool anyser, bool self, R acc[3],
+                                          const R *twn = nullptr) {
     const R dx = d[0], dy = d[1], dz = d[2];
     R k1, k2, k3, k4;
     if (NEAR) {
@@ -181,6 +184,21 @@ __device__ __forceinline__ void pair_term(const R d[3], const R r2, const R dt[3
         const R uy = (s0.x - dt[0]) * dx + (s0.y - dt[1]) * dy + (s0.z - dt[2]) * dz;
         const R yn = dx * sw.x + dy * sw.y + dz * sw.z;
         const R b = uy * yn * k4;
+        acc[0] += b * dx;
+        acc[1] += b * dy;
+        acc[2] += b * dz;
+    } else if (OP == OP_LDLT) {
+        // transpose of D^L: k2 [ (yhat . w_i n_i) v_j + (yhat . w_j n_j) v_i ]
+        const R ynt = dx * twn[0] + dy * twn[1] + dz * twn[2];
+        const R yns = dx * sw.x + dy * sw.y + dz * sw.z;
+        acc[0] += k2 * (ynt * s0.x + yns * dt[0]);
+    } else if (OP == OP_SDLT) {
+        // transpose of D^S: k4 yhat [ (yhat . w_i n_i)(yhat . v_j) + (yhat . w_j n_j)(yhat . v_i) ]
+        const R ynt = dx * twn[0] + dy * twn[1] + dz * twn[2];
+        const R yns = dx * sw.x + dy * sw.y + dz * sw.z;
+        const R yvs = dx * s0.x + dy * s0.y + dz * s0.z;
+        const R yvt = dx * dt[0] + dy * dt[1] + dz * dt[2];
+        const R b = k4 * (ynt * yvs + yns * yvt);
         acc[0] += b * dx;
         acc[1] += b * dy;
         acc[2] += b * dz;
@@ -243,7 +261,8 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         part_base = (int64_t)blockIdx.y * NC * NSL * a.n_pad;
         pstride = a.n_pad;
     }
-    R y[TPT][3], dt[TPT][3];
+    constexpr bool TR = (OP == OP_LDLT || OP == OP_SDLT);
+    R y[TPT][3], dt[TPT][3], twn[TPT][3];
     Acc<R> acc[TPT][NC];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
@@ -252,6 +271,10 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         y[t][0] = p.x; y[t][1] = p.y; y[t][2] = p.z;
         const V4 d = d0[i];
         dt[t][0] = d.x; dt[t][1] = d.y; dt[t][2] = d.z;
+        if (TR) {
+            const V4 q = a.wn[i];
+            twn[t][0] = q.x; twn[t][1] = q.y; twn[t][2] = q.z;
+        }
     }
 
     for (int64_t tile = s_beg; tile < s_end; tile += kTile) {
@@ -289,12 +312,12 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
 #pragma unroll
                 for (int t = 0; t < TPT; ++t) {
                     const bool self = (js == tbase + threadIdx.x + t * TPB);
-                    pair_term<R, OP, true>(d[t], r2[t], dt[t], sw, s0, s1, c, anyser, self, part[t]);
+                    pair_term<R, OP, true>(d[t], r2[t], dt[t], sw, s0, s1, c, anyser, self, part[t], twn[t]);
                 }
             } else {
 #pragma unroll
                 for (int t = 0; t < TPT; ++t)
-                    pair_term<R, OP, false>(d[t], r2[t], dt[t], sw, s0, s1, c, false, false, part[t]);
+                    pair_term<R, OP, false>(d[t], r2[t], dt[t], sw, s0, s1, c, false, false, part[t], twn[t]);
             }
         }
 #pragma unroll
@@ -616,6 +639,7 @@ struct PackArgs {
     const d4 *pos64;          // layout positions and weights (sorted order)
     const d4 *wn64;           // layout weighted normals (sorted order)
     double s0, s1;            // scale of d0, d1 records (fused ops)
+    int no_weight;            // single layers: pack the density without w (transpose)
     void *out0, *out1;        // float4 or d4 [n_pad]
     double *wdot_part;        // optional: per-block partial of sum w * d0 (Darcy gauge)
 };
@@ -629,9 +653,15 @@ __global__ void pack_kernel(const PackArgs a) {
         const int32_t o = a.perm[i];
         V4 r0 = {R(0), R(0), R(0), R(0)}, r1 = {R(0), R(0), R(0), R(0)};
         if (o >= 0) {
-            const double w = a.pos64[i].w;
+            const double w = a.no_weight ? 1.0 : a.pos64[i].w;
             switch (a.op) {
                 case OP_LSL: r0.x = R(a.s0 * w * a.d0[o]); break;
+                case OP_LDLT: r0.x = R(a.s0 * a.d0[o]); break;
+                case OP_SDLT:
+                    r0.x = R(a.s0 * a.d0[o]);
+                    r0.y = R(a.s0 * a.d0[a.n + o]);
+                    r0.z = R(a.s0 * a.d0[2 * a.n + o]);
+                    break;
                 case OP_LDL: r0.x = R(a.s0 * a.d0[o]); wd = w * a.d0[o]; break;
                 case OP_SSL:
                     r0.x = R(a.s0 * w * a.d0[o]);
@@ -676,6 +706,7 @@ __global__ void pack_kernel(const PackArgs a) {
 
 // ------------------------------------------------------------------ epilogue
 struct EpiArgs {
+    int weight_out;          // multiply the pair sum by the target weight (single-layer transpose)
     const int32_t *perm;
     int64_t n, n_pad;
     int nc, nsplit, nslot;   // nslot: 2 for FP32 (hi, lo), 1 for FP64
@@ -730,7 +761,7 @@ __global__ void epilogue_kernel(const EpiArgs a) {
             s += reinterpret_cast<const double *>(a.part)[base];
         }
     }
-    double v = a.scale * s;
+    double v = a.scale * s * (a.weight_out ? a.pos64[i].w : 1.0);
     if (a.self_src) v += a.self_coef * a.pos64[i].w * a.self_src[(int64_t)q * a.n + o];
     double r = a.a_op * v + extra + (q == 0 ? a.add0 : (q == 1 ? a.add1 : a.add2));
     if (a.rank1_nrm) r += rank1 * a.rank1_nrm[(int64_t)q * a.n + o];
@@ -753,6 +784,14 @@ cudaError_t launch_pair_op64(int op, dim3 grid, const KArgs<double> &ka, cudaStr
         case OP_SSLDL: return launch64<OP_SSLDL>(grid, ka, s);
         default: return launch64<OP_LSLDL>(grid, ka, s);
     }
+}
+
+// transposed double layers run on the generic kernel in both precisions
+template <typename R>
+cudaError_t launch_transpose(int op, dim3 grid, const KArgs<R> &ka, cudaStream_t s) {
+    if (op == OP_LDLT) pair_kernel<R, OP_LDLT, kTPB64, kTPT64><<<grid, kTPB64, 0, s>>>(ka);
+    else pair_kernel<R, OP_SDLT, kTPB64, kTPT64><<<grid, kTPB64, 0, s>>>(ka);
+    return cudaGetLastError();
 }
 
 template <int OP>
@@ -779,6 +818,8 @@ int kernel_class(int op) {
         case OP_SSL: return SSD_K_STOKES_SL;
         case OP_SDL: return SSD_K_STOKES_DL;
         case OP_SSLDL: return SSD_K_STOKES_SLDL;
+        case OP_LDLT: return SSD_K_LAPLACE_DL_T;
+        case OP_SDLT: return SSD_K_STOKES_DL_T;
         default: return SSD_K_LAPLACE_SLDL;
     }
 }
@@ -948,14 +989,16 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const int nc = op_components(op);
     const bool f32 = (pc.prec == SSD_FP32C);
     const int64_t n = L.n, n_pad = L.n_pad;
-    const int tspan = f32 ? kTPB32 * kTPT32 : kTPB64 * kTPT64;
+    const bool transposed = (op == OP_LDLT || op == OP_SDLT);
+    const bool packed32 = f32 && !transposed;    // the packed FP32 kernel, else the generic one
+    const int tspan = packed32 ? kTPB32 * kTPT32 : kTPB64 * kTPT64;
     const int64_t ntiles_t = n_pad / tspan;
     const int64_t ntiles_s = n_pad / kTile;
     // splits: enough CTAs for several waves of resident CTAs, so that the
     // uneven cost of near and far target tiles evens out (FP32C: tuned on the
     // h = 1/32 sphere, where it reaches one 128-source tile per CTA)
-    const int occ = f32 ? ctx->occ32 : ctx->occ64;
-    int64_t want = (int64_t)ctx->num_sms * occ * (f32 ? ctx->waves32 : 2);
+    const int occ = packed32 ? ctx->occ32 : ctx->occ64;
+    int64_t want = (int64_t)ctx->num_sms * occ * (packed32 ? ctx->waves32 : 2);
     int64_t nsplit = (want + ntiles_t - 1) / ntiles_t;
     if (nsplit < 1) nsplit = 1;
     if (nsplit > ntiles_s) nsplit = ntiles_s;
@@ -993,6 +1036,8 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
             s1 = pc.alpha / (8.0 * kPi * pc.mu);        // w f records
             self_coef = s1 * sig1_0 / pc.delta; self_src = pc.dens1;
             break;
+        case OP_LDLT: scale = 1.0 / (4.0 * kPi); break;
+        case OP_SDLT: scale = -6.0 / (8.0 * kPi); break;
         default:  // OP_LSLDL
             scale = -1.0 / (4.0 * kPi);
             s0 = pc.beta;                                // p records
@@ -1000,11 +1045,13 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
             self_coef = scale * pc.alpha * sig1_0 / pc.delta; self_src = pc.dens1;
             break;
     }
+    const bool tsl = pc.transpose_sl && (op == OP_LSL || op == OP_SSL);
 
-    PackArgs pa;
+    PackArgs pa{};
     pa.perm = L.perm; pa.n = n; pa.n_pad = n_pad; pa.op = op;
     pa.d0 = pc.dens0; pa.d1 = pc.dens1; pa.pos64 = L.pos64; pa.wn64 = L.wn64; pa.s0 = s0; pa.s1 = s1;
     pa.out0 = base + o_d0; pa.out1 = two_rec ? base + o_d1 : nullptr;
+    pa.no_weight = tsl ? 1 : 0;
     const bool rank1 = pc.rank1_weight_mean || pc.rank1_nrm != nullptr;
     pa.wdot_part = rank1 ? reinterpret_cast<double *>(base + o_wdot) : nullptr;
     if (f32) pack_kernel<float4, float><<<pack_blocks, 256, 0, s>>>(pa);
@@ -1017,7 +1064,17 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     SSD_TRY(timed_begin(ctx, s, &ev));
     dim3 grid((unsigned)ntiles_t, (unsigned)nsplit);
     cudaError_t e;
-    if (f32) {
+    if (f32 && transposed) {
+        KArgs<float> ka;
+        ka.pos = L.pos32; ka.wn = L.wn32;
+        ka.d0 = reinterpret_cast<const float4 *>(base + o_d0);
+        ka.d1 = ka.d0;
+        ka.n_pad = n_pad; ka.chunk = chunk;
+        ka.c = make_consts<float>(pc.delta, kRhoFar32);
+        ka.part = reinterpret_cast<float *>(base + o_part);
+        ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+        e = launch_transpose<float>(op, grid, ka, s);
+    } else if (f32) {
         K32Args ka;
         ka.pos = L.pos32; ka.wn = L.wn32; ka.cbox = L.cbox;
         ka.d0 = reinterpret_cast<const float4 *>(base + o_d0);
@@ -1036,13 +1093,13 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.c = make_consts<double>(pc.delta, kRhoFar64);
         ka.part = reinterpret_cast<double *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
-        e = launch_pair_op64(op, grid, ka, s);
+        e = transposed ? launch_transpose<double>(op, grid, ka, s) : launch_pair_op64(op, grid, ka, s);
     }
     ctx->launches++;
     if (e != cudaSuccess) return cuda_check(ctx, e, "pair kernel launch");
     timed_end(ctx, s, ev, cls, pc.prec, (double)n * (double)n);
 
-    EpiArgs ea;
+    EpiArgs ea{};
     ea.perm = L.perm; ea.n = n; ea.n_pad = n_pad; ea.nc = nc; ea.nsplit = (int)nsplit; ea.nslot = nslot;
     ea.part_is_float = f32 ? 1 : 0; ea.part = base + o_part;
     ea.scale = scale; ea.self_coef = self_coef; ea.self_src = self_src; ea.pos64 = L.pos64;
@@ -1051,6 +1108,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     ea.wdot_part = rank1 ? reinterpret_cast<const double *>(base + o_wdot) : nullptr;
     ea.nwdot = pack_blocks; ea.wdot_scale = rank1 ? 1.0 / L.wsum : 0.0;
     ea.rank1_nrm = pc.rank1_nrm;
+    ea.weight_out = tsl ? 1 : 0;
     ea.out = pc.out;
     epilogue_kernel<<<(unsigned)((n_pad * nc + 127) / 128), 128, 0, s>>>(ea);
     ctx->launches++;
@@ -1173,7 +1231,7 @@ int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cu
             break;
     }
     const bool rank1 = pc.rank1_weight_mean || pc.rank1_nrm != nullptr;
-    BPackArgs pa;
+    BPackArgs pa{};
     pa.perm = B.L.perm; pa.n_total = n; pa.n_pad = n_pad; pa.op = op;
     pa.d0 = pc.dens0; pa.d1 = pc.dens1;
     pa.nc0 = (op == OP_LSL || op == OP_LDL || op == OP_LSLDL) ? 1 : 3;
@@ -1232,7 +1290,7 @@ int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cu
     for (int k = 0; k < B.nsurf; ++k) pairs += (double)B.n[k] * (double)B.n[k];
     timed_end(ctx, s, ev, kernel_class(op), pc.prec, pairs * nrhs);
 
-    BEpiArgs ea;
+    BEpiArgs ea{};
     ea.perm = B.L.perm; ea.elem_surf = B.elem_surf; ea.surfs = reinterpret_cast<const BSurf *>(B.surfs[pr]);
     ea.n_total = n; ea.n_pad = n_pad; ea.nc = nc; ea.nslot = nslot; ea.part_is_float = f32 ? 1 : 0;
     ea.nrhs = nrhs; ea.nsurf = B.nsurf; ea.part = base + o_part; ea.part_stride = part_stride;
@@ -1377,7 +1435,7 @@ extern "C" int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double
     const unsigned nb = (unsigned)((n_pad + 255) / 256);
     noalloc_layout_kernel<<<nb, 256, 0, s>>>(pts->xyz, pts->nrm, pts->w, n, n_pad, L);
     noalloc_chunk_box_kernel<<<(unsigned)((n_pad / kChunk + 127) / 128), 128, 0, s>>>(L);
-    PackArgs pa;
+    PackArgs pa{};
     pa.perm = L.perm; pa.n = n; pa.n_pad = n_pad; pa.op = OP_SDL;
     pa.d0 = u; pa.d1 = nullptr; pa.pos64 = L.pos64; pa.wn64 = L.wn64; pa.s0 = 1.0; pa.s1 = 1.0;
     pa.out0 = d0; pa.out1 = nullptr; pa.wdot_part = nullptr;
@@ -1395,7 +1453,7 @@ extern "C" int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double
     ctx->launches++;
     SSD_TRY(launch_check(ctx, "no-alloc pair kernel"));
 
-    EpiArgs ea;
+    EpiArgs ea{};
     ea.perm = L.perm; ea.n = n; ea.n_pad = n_pad; ea.nc = 3; ea.nsplit = (int)nsplit; ea.nslot = 2;
     ea.part_is_float = 1; ea.part = part;
     ea.scale = 6.0 / (8.0 * kPi); ea.self_coef = 0.0; ea.self_src = nullptr; ea.pos64 = L.pos64;

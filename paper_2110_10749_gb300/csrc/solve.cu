@@ -665,6 +665,324 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     return status;
 }
 
+// ------------------------------------------------------------------- adjoint
+// Discrete adjoint of the interface solve.  With the sweep written as
+//   p = P_g A_D^{-1} (mu/kappa) L q            (Darcy, gauge projection P_g)
+//   u = A_S^{-1} (U_inf + M(n p) - M f_x)      (Stokes, f_x = explicit traction part)
+//   q = n . u                                  (fixed point of the interface map)
+// the interface map is q = T q + t0 with T = N^T A_S^{-1} M N P_g A_D^{-1} (mu/kappa) L.
+// For a functional J(q, p, u; theta) the derivative in a parameter theta is
+//   dJ/dtheta = dJ/dtheta|explicit + g_p . dp/dtheta|_q + nu . X_theta,
+//   X_theta = d(U_inf + M(n p) - M f_x)/dtheta|_q - (dA_S/dtheta) u,
+//   nu = A_S^{-T} (n lambda) + mu_u,  (I - T)^T lambda = zeta,
+// where mu_u = A_S^{-T} g_u and zeta collects dJ/dq and the adjoint Darcy
+// term (mu/kappa) L^T A_D^{-T} P_g^T (g_p + N^T M^T mu_u).  All transposes are
+// those of the weighted discrete operators (transposed pair kernels).
+
+// y = v n (scalar field times the normal field)
+__global__ void scal_normal_kernel(int64_t n, const double *v, const double *nrm, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) y[k * n + i] = v[i] * nrm[k * n + i];
+}
+// s = n . y (vector field dotted with the normal)
+__global__ void dot_normal_kernel(int64_t n, const double *y, const double *nrm, double *s) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s[i] = y[i] * nrm[i] + y[n + i] * nrm[n + i] + y[2 * n + i] * nrm[2 * n + i];
+}
+// y += f * (*d) * x  (device scalar)
+__global__ void axpy_dev_kernel(int64_t n, const double *d, double f, const double *x, double *y) {
+    const double a = f * (*d);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+__global__ void fill_kernel(int64_t n, double v, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+// kind 0: y = w (e . x)   (weights of the flux moment)
+// kind 1: y = -w (n . e)  (pressure weights of the drag along e)
+__global__ void weight_field_kernel(int64_t n, const double *w, const double *xyz, const double *nrm, double e0,
+                                    double e1, double e2, int kind, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (kind == 0) y[i] = w[i] * (e0 * xyz[i] + e1 * xyz[n + i] + e2 * xyz[2 * n + i]);
+        else y[i] = -w[i] * (e0 * nrm[i] + e1 * nrm[n + i] + e2 * nrm[2 * n + i]);
+    }
+}
+// y = c w (e - (e . n) n)
+__global__ void weighted_tangent_kernel(int64_t n, const double *w, const double *nrm, double c, double e0, double e1,
+                                        double e2, double *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double en = e0 * nrm[i] + e1 * nrm[n + i] + e2 * nrm[2 * n + i];
+        y[i] = c * w[i] * (e0 - en * nrm[i]);
+        y[n + i] = c * w[i] * (e1 - en * nrm[n + i]);
+        y[2 * n + i] = c * w[i] * (e2 - en * nrm[2 * n + i]);
+    }
+}
+// d/dlog(kappa) of the exact-velocity part a e_r + f_theta e_theta of the
+// porous-sphere benchmark traction (traction_jt_kernel), c = 2 + kappa/R^2:
+//   da/dlog(kappa)      = -24 mu U kappa cos(theta) / (R^3 c^2),
+//   d(b)/dlog(kappa)    = -(3 mu U/R) 3 kappa/(R^2 c^2)  for f_theta = b sin(theta).
+__global__ void jt_dtraction_kernel(int64_t n, const double *xyz, double R, double kappa, double mu, double U, double e0,
+                                    double e1, double e2, double *y) {
+    const double c = 2.0 + kappa / (R * R);
+    const double db = -(3.0 * mu * U / R) * 3.0 * kappa / (R * R * c * c);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = xyz[i], yy = xyz[n + i], z = xyz[2 * n + i];
+        const double r = sqrt(x * x + yy * yy + z * z);
+        const double er0 = x / r, er1 = yy / r, er2 = z / r;
+        const double ct = (e0 * x + e1 * yy + e2 * z) / r;
+        const double da = -24.0 * mu * U * kappa * ct / (R * R * R * c * c);
+        y[i] = da * er0 + db * (ct * er0 - e0);
+        y[n + i] = da * er1 + db * (ct * er1 - e1);
+        y[2 * n + i] = da * er2 + db * (ct * er2 - e2);
+    }
+}
+
+struct Adjoint {
+    ssd_ctx *ctx;
+    const ssd_points *pts;
+    const Layout *L;
+    ssd_ddm_params P;
+    cudaStream_t s;
+    int64_t n;
+    double c;          // BJS slip coefficient of A_S (0 unless implicit BJS)
+    int nonconv = 0;
+    Dots dots;
+    Buf scal, ones, t3a, t3b, t1a, w3, w3b, w1, w1b;
+
+    int init() {
+        SSD_TRY(dots.init(ctx, s, 1));
+        SSD_TRY(scal.alloc(ctx, sizeof(double) * 8));
+        SSD_TRY(ones.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(t3a.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(t3b.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(t1a.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(w3.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(w3b.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(w1.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(w1b.alloc(ctx, sizeof(double) * n));
+        fill_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, ones.d());
+        ctx->launches++;
+        return launch_check(ctx, "adjoint init");
+    }
+    // y = a_op * op(x) [+ a_id * xin]; tsl: transposed single layer
+    int apply(int op, bool tsl, const double *x, double *y, double a_op = 1.0, const double *xin = nullptr,
+              double a_id = 0.0) {
+        PairCall pc;
+        pc.op = op; pc.transpose_sl = tsl; pc.prec = P.inner.prec; pc.delta = P.delta; pc.mu = P.mu;
+        pc.dens0 = x; pc.a_op = a_op; pc.xin = xin; pc.a_id = a_id; pc.out = y;
+        return pair_apply(ctx, *L, pc, s);
+    }
+    // *dst = sum_i v_i
+    int sum(const double *v, double *dst) { return dots.multi(v, 0, 1, ones.d(), n, dst); }
+    // a . b to the host
+    int hdot(const double *a, const double *b, int64_t m, double *host) {
+        SSD_TRY(dots.multi(a, 0, 1, b, m, scal.d() + 4));
+        return read_scalars(ctx, scal.d() + 4, 1, host, s);
+    }
+    // A_S^T y = y - (D^S)^T y + c P M^T y [+ (w n)(sum_i n_i . y_i)/W when deflating]
+    int AsT(const double *y, double *out) {
+        SSD_TRY(apply(OP_SDLT, false, y, out, -1.0, y, 1.0));
+        if (c != 0.0) {
+            SSD_TRY(apply(OP_SSL, true, y, t3a.d()));
+            tangential_kernel<<<grid_for(n), 256, 0, s>>>(n, t3a.d(), pts->nrm, t3b.d());
+            axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, c, t3b.d(), 1.0, out);
+            ctx->launches += 2;
+        }
+        if (P.inner.deflate) {
+            dot_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, y, pts->nrm, t1a.d());
+            ctx->launches++;
+            SSD_TRY(sum(t1a.d(), scal.d()));
+            scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->nrm, t3b.d());
+            axpy_dev_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, scal.d(), 1.0 / L->wsum, t3b.d(), out);
+            ctx->launches += 2;
+        }
+        return launch_check(ctx, "A_S^T");
+    }
+    // A_D^T v = -(D^L)^T v + w (sum_j v_j)/W
+    int AdT(const double *v, double *out) {
+        SSD_TRY(apply(OP_LDLT, false, v, out, -1.0));
+        SSD_TRY(sum(v, scal.d() + 1));
+        axpy_dev_kernel<<<grid_for(n), 256, 0, s>>>(n, scal.d() + 1, 1.0 / L->wsum, pts->w, out);
+        ctx->launches++;
+        return launch_check(ctx, "A_D^T");
+    }
+    int solve(int64_t m, const MatVec &A, const double *rhs, double *x) {
+        GmresResult r;
+        const int st = gmres(ctx, s, m, A, rhs, x, P.inner.tol, P.inner.restart, P.inner.maxit, false, &r);
+        if (st == SSD_ENOTCONV) { nonconv++; return SSD_OK; }
+        return st;
+    }
+    int solveAsT(const double *rhs, double *x) {
+        return solve(3 * n, [&](const double *in, double *o) -> int { return AsT(in, o); }, rhs, x);
+    }
+    int solveAdT(const double *rhs, double *x) {
+        return solve(n, [&](const double *in, double *o) -> int { return AdT(in, o); }, rhs, x);
+    }
+    // P_g^T v = v - w (sum_j v_j)/W  (in place)
+    int PgT(double *v) {
+        SSD_TRY(sum(v, scal.d() + 2));
+        axpy_dev_kernel<<<grid_for(n), 256, 0, s>>>(n, scal.d() + 2, -1.0 / L->wsum, pts->w, v);
+        ctx->launches++;
+        return launch_check(ctx, "P_g^T");
+    }
+    // out = (mu/kappa) L^T A_D^{-T} P_g^T N^T h   (h: a 3n field, N^T h = n . h)
+    int darcy_adjoint(const double *h3, double *out) {
+        dot_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, h3, pts->nrm, w1.d());
+        ctx->launches++;
+        SSD_TRY(PgT(w1.d()));
+        SSD_TRY(solveAdT(w1.d(), w1b.d()));
+        return apply(OP_LSL, true, w1b.d(), out, P.mu / P.kappa);
+    }
+    // out = v - T^T v, T^T v = (mu/kappa) L^T A_D^{-T} P_g^T N^T M^T A_S^{-T} (n v)
+    int interface_matvec(const double *v, double *out) {
+        scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, v, pts->nrm, w3.d());
+        ctx->launches++;
+        SSD_TRY(solveAsT(w3.d(), w3b.d()));
+        SSD_TRY(apply(OP_SSL, true, w3b.d(), w3.d()));
+        SSD_TRY(darcy_adjoint(w3.d(), out));
+        axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, v, -1.0, out);
+        ctx->launches++;
+        return launch_check(ctx, "adjoint interface matvec");
+    }
+};
+
+int ddm_gradient_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional, double *value,
+                      double grad[2], cudaStream_t s) {
+    SSD_TRY(check_ddm(ctx, prm));
+    if (!prm->outer_gmres) return set_error(ctx, SSD_EINVAL, "gradients need the interface GMRES (outer_gmres = 1)");
+    const bool jt = prm->traction_mode == SSD_TRACTION_JOSEPH_TAO;
+    const bool implicit = prm->traction_mode == SSD_TRACTION_BJS && prm->bjs_implicit;
+    if (!jt && !implicit && prm->gamma != 0.0)
+        return set_error(ctx, SSD_EINVAL, "gradients need bjs_implicit = 1 in BJS mode with gamma != 0");
+    if (functional != SSD_FUNC_DRAG && functional != SSD_FUNC_FLUX)
+        return set_error(ctx, SSD_EINVAL, "unknown functional");
+    if (prm->inner.use_sa) return set_error(ctx, SSD_EINVAL, "gradients need GMRES local solves (use_sa = 0)");
+    const int64_t n = pts->n;
+    // forward solve
+    Buf q, p, u;
+    SSD_TRY(q.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(p.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(u.alloc(ctx, sizeof(double) * 3 * n));
+    double drag[3];
+    int its = 0;
+    int status = ddm_impl(ctx, pts, prm, q.d(), p.d(), u.d(), nullptr, drag, &its, nullptr, nullptr, s);
+    if (status != SSD_OK && status != SSD_ENOTCONV) return status;
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    Adjoint A;
+    A.ctx = ctx; A.pts = pts; A.L = lref.L; A.P = *prm; A.s = s; A.n = n;
+    A.c = implicit ? prm->bjs_sign * prm->gamma / sqrt(prm->kappa) : 0.0;
+    SSD_TRY(A.init());
+    const double U = sqrt(prm->uinf[0] * prm->uinf[0] + prm->uinf[1] * prm->uinf[1] + prm->uinf[2] * prm->uinf[2]);
+    const double e0 = U > 0 ? prm->uinf[0] / U : 0.0, e1 = U > 0 ? prm->uinf[1] / U : 0.0,
+                 e2 = U > 0 ? prm->uinf[2] / U : 1.0;
+    double h = 0.0, g0 = 0.0, g1 = 0.0, val = 0.0;
+
+    // X_theta for theta = log(kappa) (X0) and gamma (X1).  At fixed q the
+    // Darcy pressure scales as 1/kappa, so dp/dlog(kappa)|_q = -p.
+    Buf X0, X1, t3, t3b, pu;
+    SSD_TRY(X0.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(X1.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(t3.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(t3b.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(pu.alloc(ctx, sizeof(double) * 3 * n));
+    scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, p.d(), pts->nrm, t3.d());
+    ctx->launches++;
+    SSD_TRY(A.apply(OP_SSL, false, t3.d(), X0.d(), -1.0));                 // -M(n p)
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(X1.d(), 0, sizeof(double) * 3 * n, s), "memset"));
+    if (A.c != 0.0) {
+        // dA_S/dlog(kappa) = -(c/2) M P,  dA_S/dgamma = (c/gamma) M P
+        tangential_kernel<<<grid_for(n), 256, 0, s>>>(n, u.d(), pts->nrm, pu.d());
+        ctx->launches++;
+        SSD_TRY(A.apply(OP_SSL, false, pu.d(), t3b.d()));                  // M P u
+        axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, 0.5 * A.c, t3b.d(), 1.0, X0.d());
+        axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, -A.c / prm->gamma, t3b.d(), 0.0, X1.d());
+        ctx->launches += 2;
+    }
+    if (jt) {
+        // the benchmark right-hand side holds -M(a e_r + f_theta e_theta)
+        jt_dtraction_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->xyz, prm->radius, prm->kappa, prm->mu, U, e0, e1, e2,
+                                                       t3.d());
+        ctx->launches++;
+        SSD_TRY(A.apply(OP_SSL, false, t3.d(), X0.d(), -1.0, X0.d(), 1.0));
+    }
+    SSD_TRY(launch_check(ctx, "adjoint sources"));
+
+    // zeta = dJ/dq + Darcy adjoint of the pressure sensitivity; nu_extra = mu_u
+    Buf zeta, lam, nu, mu_u;
+    SSD_TRY(zeta.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(lam.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(nu.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(mu_u.alloc(ctx, sizeof(double) * 3 * n));
+    if (functional == SSD_FUNC_FLUX) {
+        // J = sum_i w_i q_i (e . x_i)
+        weight_field_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->xyz, pts->nrm, e0, e1, e2, 0, zeta.d());
+        ctx->launches++;
+        SSD_TRY(A.hdot(zeta.d(), q.d(), n, &val));
+        SSD_TRY(cuda_check(ctx, cudaMemsetAsync(mu_u.d(), 0, sizeof(double) * 3 * n, s), "memset"));
+    } else {
+        // J = e . sum_i w_i f_i = g_p . p + g_u . u + explicit terms
+        val = drag[0] * e0 + drag[1] * e1 + drag[2] * e2;
+        Buf gp;
+        SSD_TRY(gp.alloc(ctx, sizeof(double) * n));
+        weight_field_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->xyz, pts->nrm, e0, e1, e2, 1, gp.d());
+        ctx->launches++;
+        SSD_TRY(A.hdot(gp.d(), p.d(), n, &h));
+        g0 -= h;                                                             // g_p . dp/dlog(kappa)|_q
+        if (A.c != 0.0) {
+            // g_u = c w P e;  explicit: (dc/dtheta) sum_i w_i (P u_i) . e
+            weighted_tangent_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->nrm, A.c, e0, e1, e2, t3.d());
+            ctx->launches++;
+            SSD_TRY(A.solveAsT(t3.d(), mu_u.d()));
+            SSD_TRY(A.hdot(pu.d(), t3.d(), 3 * n, &h));                     // c sum w (P u) . e
+            g0 += -0.5 * h;
+            g1 += h / prm->gamma;
+        } else {
+            SSD_TRY(cuda_check(ctx, cudaMemsetAsync(mu_u.d(), 0, sizeof(double) * 3 * n, s), "memset"));
+        }
+        if (jt) {
+            // explicit: e . sum_i w_i d(a e_r + f_theta e_theta)/dlog(kappa)
+            jt_dtraction_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->xyz, prm->radius, prm->kappa, prm->mu, U, e0, e1,
+                                                           e2, t3.d());
+            ctx->launches++;
+            const double ek[3] = {e0, e1, e2};
+            for (int k = 0; k < 3; ++k) {
+                if (ek[k] == 0.0) continue;
+                SSD_TRY(A.hdot(t3.d() + k * n, pts->w, n, &h));
+                g0 += ek[k] * h;
+            }
+        }
+        // zeta = (mu/kappa) L^T A_D^{-T} P_g^T (g_p + N^T M^T mu_u)
+        SSD_TRY(A.apply(OP_SSL, true, mu_u.d(), t3b.d()));
+        scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, gp.d(), pts->nrm, t3.d());
+        axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, 1.0, t3.d(), 1.0, t3b.d());   // n g_p + M^T mu_u
+        ctx->launches += 2;
+        SSD_TRY(A.darcy_adjoint(t3b.d(), zeta.d()));
+    }
+    // interface adjoint (I - T)^T lambda = zeta, then nu = A_S^{-T}(n lambda) + mu_u
+    {
+        GmresResult r;
+        const int m = prm->maxit_outer < 128 ? prm->maxit_outer : 128;
+        auto M = [&](const double *v, double *o) -> int { return A.interface_matvec(v, o); };
+        const int st = gmres(ctx, s, n, M, zeta.d(), lam.d(), prm->tol_outer, m, prm->maxit_outer, false, &r);
+        if (st == SSD_ENOTCONV) A.nonconv++;
+        else SSD_TRY(st);
+        scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, lam.d(), pts->nrm, t3.d());
+        ctx->launches++;
+        SSD_TRY(A.solveAsT(t3.d(), nu.d()));
+        axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, 1.0, mu_u.d(), 1.0, nu.d());
+        ctx->launches++;
+    }
+    SSD_TRY(A.hdot(nu.d(), X0.d(), 3 * n, &h)); g0 += h;
+    SSD_TRY(A.hdot(nu.d(), X1.d(), 3 * n, &h)); g1 += h;
+    if (value) *value = val;
+    grad[0] = g0;
+    grad[1] = g1;
+    if (A.nonconv && status == SSD_OK) status = set_error(ctx, SSD_ENOTCONV, "iteration limit reached in an adjoint solve");
+    return status;
+}
+
 int op_entry(ssd_ctx *ctx, const ssd_points *pts, const PairCall &pc, cudaStream_t s) {
     if (!finite_pos(pc.delta)) return set_error(ctx, SSD_EINVAL, "delta must be positive and finite");
     if (!finite_pos(pc.mu)) return set_error(ctx, SSD_EINVAL, "mu must be positive and finite");
@@ -742,6 +1060,21 @@ int ssd_laplace_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, const do
     return op_entry(ctx, pts, pc, (cudaStream_t)stream);
 }
 
+int ssd_apply_transpose(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu, const double *dens,
+                        double *out, int prec, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    PairCall pc;
+    switch (op) {
+        case SSD_OP_LAPLACE_SL: pc.op = OP_LSL; pc.transpose_sl = true; break;
+        case SSD_OP_LAPLACE_DL: pc.op = OP_LDLT; break;
+        case SSD_OP_STOKES_SL: pc.op = OP_SSL; pc.transpose_sl = true; break;
+        case SSD_OP_STOKES_DL: pc.op = OP_SDLT; break;
+        default: return set_error(ctx, SSD_EINVAL, "transpose: op must be a single or double layer");
+    }
+    pc.prec = prec; pc.delta = delta; pc.mu = mu; pc.dens0 = dens; pc.out = out;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
 int ssd_darcy_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, double kappa, const double *q,
                     double *p_out, const ssd_krylov *kr, int *iters, double *relres, ssd_stream stream) {
     if (!ctx) return SSD_EINVAL;
@@ -788,6 +1121,14 @@ int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     return ddm_impl(ctx, pts, prm, q, p_D, u_S, f_S, drag, outer_its, inner_its, res_hist, (cudaStream_t)stream);
+}
+
+int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional, double *value,
+                     double grad[2], ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!grad) return set_error(ctx, SSD_EINVAL, "grad is NULL");
+    return ddm_gradient_impl(ctx, pts, prm, functional, value, grad, (cudaStream_t)stream);
 }
 
 int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double *nrm, const double *w,
