@@ -87,8 +87,12 @@ def test_batched_ddm_matches_single_surface_solves(gpu_ctx, batch):
                     a = rb[k][r][..., sl].cpu().numpy().reshape(r1[k].shape)
                     b = r1[k].cpu().numpy()
                     assert np.linalg.norm(a - b) / np.linalg.norm(b) < tol, (prec, k, r, s)
-                # drag components that vanish by symmetry differ at the solve tolerance
-                assert np.allclose(rb["drag"][r, s], r1["drag"], rtol=tol, atol=1e-7)
+                # drag components that vanish by symmetry carry the solve noise:
+                # compare against the drag's norm (FP64 to ~10x the interface
+                # tolerance, FP32C to the pair-sum accuracy)
+                dtol = 1e-8 if prec == ssd.FP64 else tol
+                err = np.abs(rb["drag"][r, s] - r1["drag"]).max()
+                assert err <= dtol * np.linalg.norm(r1["drag"]), (prec, r, s, rb["drag"][r, s], r1["drag"])
 
 
 def test_batched_benchmark_mode_against_oracle(gpu_ctx):
