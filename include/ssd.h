@@ -90,13 +90,22 @@ int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out /* host */);
 
 /* ------------------------------------------------------------- quadrature */
 
-/* Surfaces of Section 5.4 (eqs. Sphere, Ellipsoid): level sets phi = 0 with
- * phi > 0 outside.  SPHERE uses abc[0] as the radius. */
-enum ssd_surface_kind { SSD_SPHERE = 0, SSD_ELLIPSOID = 1 };
+/* Surfaces: level sets phi = 0 with phi > 0 outside.  SPHERE and ELLIPSOID
+ * are eqs. Sphere and Ellipsoid of Section 5.4 (SPHERE uses abc[0] as the
+ * radius).  STAR is the star-shaped surface |x - c| = r(xi),
+ * r(xi) = 1 + sum_{l<=4} sum_{m=-l..l} c_lm Y_lm(xi), xi = (x - c)/|x - c|,
+ * with real orthonormal spherical harmonics (Condon-Shortley phase removed:
+ * Y_l,m = sqrt(2) (-1)^m Re Y_l^m for m > 0, sqrt(2) (-1)^m Im Y_l^|m| for
+ * m < 0) and clm[k], k = l^2 + l + m, 25 coefficients; phi = (|x - c| - 1) -
+ * sum_k c_k Y_k(xi).  The sum of |c_lm| sqrt((2l+1)/(4 pi)) must be < 1.
+ * The paper's own examples are the sphere and the ellipsoid; star surfaces
+ * are smooth test shapes of the same construction. */
+enum ssd_surface_kind { SSD_SPHERE = 0, SSD_ELLIPSOID = 1, SSD_STAR = 2 };
 typedef struct {
     int kind;
     double center[3];
-    double abc[3];     /* semi-axes (ELLIPSOID); abc[0] = R (SPHERE) */
+    double abc[3];       /* semi-axes (ELLIPSOID); abc[0] = R (SPHERE) */
+    const double *clm;   /* host [25] (STAR only; may be NULL otherwise) */
 } ssd_surface;
 
 /*
@@ -107,7 +116,14 @@ typedef struct {
  * psi_i(n) h^2 / |n_i|, with psi_i = b(acos|n_i|/theta) / sum_j b(acos|n_j|/theta),
  * b(r) = exp(r^2/(r^2-1)) for |r| < 1 (theta = angle_deg in radians).
  * Order: axis 0,1,2; j1 ascending; j2 ascending; smaller root first.
- * meta[4][n] = (axis, j1, j2, branch) with branch 0 for the smaller root.
+ * meta[4][n] = (axis, j1, j2, ordinal of the crossing along its line).
+ * Sphere and ellipsoid roots are closed forms.  Star-surface roots follow a
+ * fixed procedure: with Rb = 1 + sum |c_k| sqrt((2l+1)/(4 pi)), phi is sampled
+ * at t_k = t_lo + k dt, t_lo = c_i - 1.0625 Rb, dt = ((c_i + 1.0625 Rb) - t_lo)/K,
+ * K = ceil(2.125 Rb * 64); each sign change (phi > 0 against not) is bisected
+ * (mid = 0.5 (lo + hi)) until the midpoint equals an end point, and the end
+ * point with the smaller |phi| is the root.  More than 8 kept crossings on
+ * one line is an error (SSD_EINVAL).
  * Pass xyz == NULL to query the count only (*n_out).  Otherwise capacity
  * must be >= the count (else SSD_EINVAL with *n_out set to the count).
  * Points and normals are computed with correctly rounded +,-,*,/,sqrt only.
@@ -117,6 +133,21 @@ int ssd_quadrature_points(ssd_ctx *ctx, const ssd_surface *surf /* host */, doub
                           double angle_deg, int64_t capacity, int64_t *n_out /* host */,
                           double *xyz, double *nrm, double *w, int32_t *meta,
                           ssd_stream stream);
+
+/*
+ * Shape derivatives of a STAR surface's quadrature set with respect to its 25
+ * coefficients c_k, at fixed h and angle: dxyz[k][3][n], dnrm[k][3][n],
+ * dw[k][n] (device), in the order of ssd_quadrature_points; n must equal its
+ * point count.  A point moves along its grid line (dx = e_i dt); normals and
+ * weights follow from the normal formula and the partition of unity.  The
+ * set itself is held fixed: a point entering or leaving it does so with zero
+ * weight, so sums over the set stay differentiable.  The paper states no
+ * shape derivatives; these are derivatives of its quadrature rule.
+ * Synchronises `stream`.
+ */
+int ssd_quadrature_jacobian(ssd_ctx *ctx, const ssd_surface *surf /* host */, double h,
+                            double angle_deg, int64_t n, double *dxyz, double *dnrm, double *dw,
+                            ssd_stream stream);
 
 /* ----------------------------------------------------------------- points */
 

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libssd.so")
 
 SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECUDA, SSD_ENOTCONV, SSD_ENUMERIC = range(6)
 FP64, FP32C = 0, 1
-SPHERE, ELLIPSOID = 0, 1
+SPHERE, ELLIPSOID, STAR = 0, 1, 2
 TRACTION_BJS, TRACTION_JOSEPH_TAO = 0, 1
 K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_SLDL, K_LAPLACE_DL_T, K_STOKES_DL_T = range(8)
 
@@ -31,7 +31,7 @@ K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_S
 EXPORTS = [
     "ssd_ctx_create", "ssd_ctx_destroy", "ssd_status_string", "ssd_ctx_last_error",
     "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count",
-    "ssd_quadrature_points", "ssd_points_prepare", "ssd_points_release",
+    "ssd_quadrature_points", "ssd_quadrature_jacobian", "ssd_points_prepare", "ssd_points_release",
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
     "ssd_stokes_SLDL", "ssd_laplace_SLDL",
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
@@ -62,7 +62,8 @@ class CPoints(C.Structure):
 
 
 class CSurface(C.Structure):
-    _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("abc", C.c_double * 3)]
+    _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("abc", C.c_double * 3),
+                ("clm", C.POINTER(C.c_double))]
 
 
 class CKrylov(C.Structure):
@@ -117,6 +118,7 @@ def lib():
         "ssd_ctx_reset_stats": [P],
         "ssd_ctx_launch_count": [P, C.POINTER(i64)],
         "ssd_quadrature_points": [P, C.POINTER(CSurface), d, d, i64, C.POINTER(i64), P, P, P, P, P],
+        "ssd_quadrature_jacobian": [P, C.POINTER(CSurface), d, d, i64, P, P, P, P],
         "ssd_points_prepare": [P, C.POINTER(CPoints), P],
         "ssd_points_release": [P, C.POINTER(CPoints)],
         "ssd_laplace_SL": [P, C.POINTER(CPoints), d, P, P, i, P],
@@ -249,10 +251,22 @@ class Points:
         self.ctx = None
 
 
-def quadrature_points(ctx, kind, abc, h, angle_deg=70.0, center=(0.0, 0.0, 0.0)):
-    """Quadrature points of the sphere/ellipsoid (Section 5.4): dict of CUDA tensors."""
+def surface(kind, abc=(1.0,), center=(0.0, 0.0, 0.0), clm=None):
+    """ssd_surface for SPHERE (abc = (R,)), ELLIPSOID (abc = (a, b, c)) or STAR (clm[25])."""
+    abc = list(abc) if kind != STAR else []
+    cl = None
+    if kind == STAR:
+        cl = (C.c_double * 25)(*[float(v) for v in clm])
+    s = CSurface(kind, (C.c_double * 3)(*center), (C.c_double * 3)(*(abc + [0.0] * (3 - len(abc)))),
+                 C.cast(cl, C.POINTER(C.c_double)) if cl is not None else None)
+    s._keep = cl
+    return s
+
+
+def quadrature_points(ctx, kind, abc=(1.0,), h=1 / 8, angle_deg=70.0, center=(0.0, 0.0, 0.0), clm=None):
+    """Quadrature points (Section 5.4) of a sphere, ellipsoid or star surface: dict of CUDA tensors."""
     torch = _torch()
-    surf = CSurface(kind, (C.c_double * 3)(*center), (C.c_double * 3)(*(list(abc) + [0.0] * (3 - len(abc)))))
+    surf = surface(kind, abc, center, clm)
     n = C.c_int64()
     L = lib()
     ctx.check(L.ssd_quadrature_points(ctx.h, C.byref(surf), float(h), float(angle_deg), 0, C.byref(n),
@@ -267,6 +281,20 @@ def quadrature_points(ctx, kind, abc, h, angle_deg=70.0, center=(0.0, 0.0, 0.0))
                                       _ptr(xyz), _ptr(nrm), _ptr(w), C.c_void_p(meta.data_ptr()), _stream()),
               "ssd_quadrature_points")
     return {"xyz": xyz, "nrm": nrm, "w": w, "meta": meta}
+
+
+def quadrature_jacobian(ctx, clm, h, n, angle_deg=70.0, center=(0.0, 0.0, 0.0)):
+    """Derivatives of a STAR surface's points, normals and weights in its 25
+    coefficients: dict dxyz (25, 3, n), dnrm (25, 3, n), dw (25, n)."""
+    torch = _torch()
+    surf = surface(STAR, (), center, clm)
+    dev = torch.device("cuda", ctx.device)
+    dx = torch.empty((25, 3, n), dtype=torch.float64, device=dev)
+    dn = torch.empty((25, 3, n), dtype=torch.float64, device=dev)
+    dw = torch.empty((25, n), dtype=torch.float64, device=dev)
+    ctx.check(lib().ssd_quadrature_jacobian(ctx.h, C.byref(surf), float(h), float(angle_deg), int(n), _ptr(dx),
+                                            _ptr(dn), _ptr(dw), _stream()), "ssd_quadrature_jacobian")
+    return {"dxyz": dx, "dnrm": dn, "dw": dw}
 
 
 def _out_like(t, out):

@@ -22,6 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS_EXTRA = []
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
+# quadrature points are reproducible bit for bit only without FMA contraction
+FILE_FLAGS = {"quad.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -48,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *FLAGS_EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *FLAGS_EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -702,4 +702,12 @@ int ssd_quadrature_points(ssd_ctx *ctx, const ssd_surface *surf, double h, doubl
     return quadrature_points(ctx, surf, h, angle_deg, capacity, n_out, xyz, nrm, w, meta, (cudaStream_t)stream);
 }
 
+int ssd_quadrature_jacobian(ssd_ctx *ctx, const ssd_surface *surf, double h, double angle_deg, int64_t n,
+                            double *dxyz, double *dnrm, double *dw, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!surf) return set_error(ctx, SSD_EINVAL, "surface is NULL");
+    return quadrature_jacobian(ctx, surf, h, angle_deg, n, dxyz, dnrm, dw, (cudaStream_t)stream);
+}
+
 }  // extern "C"

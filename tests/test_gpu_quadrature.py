@@ -64,3 +64,62 @@ def test_size_query_and_capacity_error(gpu_ctx):
     assert st == ssd.SSD_EINVAL and n.value == 1062
     assert L.ssd_quadrature_points(gpu_ctx.h, C.byref(surf), -1.0, 70.0, 0, C.byref(n), None, None, None,
                                    None, None) == ssd.SSD_EINVAL
+
+
+STAR_CASES = [
+    (0, 1 / 16, (0.0, 0.0, 0.0)),
+    (3, 1 / 24, (0.02, -0.03, 0.01)),
+    (11, 1 / 32, (0.0, 0.0, 0.0)),
+    (-1, 1 / 20, (0.0, 0.1, 0.0)),      # -1: the unit sphere written as a star (all c = 0)
+    (40, 1 / 48, (0.0, 0.0, 0.0)),
+]
+
+
+def _clm(seed):
+    from paper_2110_10749_gb300.workloads import star_coefficients
+    return np.zeros(25) if seed < 0 else star_coefficients(seed)
+
+
+@pytest.mark.parametrize("seed,h,center", STAR_CASES)
+def test_star_points_bit_identical(gpu_ctx, seed, h, center):
+    import paper_2110_10749_gb300 as ssd
+    clm = _clm(seed)
+    g = ssd.quadrature_points(gpu_ctx, ssd.STAR, h=h, center=center, clm=clm)
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    o = Q.star_points(clm, h, 70.0, center)
+    assert g["w"].size == o["w"].size
+    assert np.array_equal(g["meta"], o["meta"])
+    assert np.array_equal(g["xyz"], o["xyz"])
+    assert np.array_equal(g["nrm"], o["nrm"])
+    assert np.abs(g["w"] - o["w"]).max() <= 1e-14 * o["w"].max()
+
+
+def test_star_rejects_large_coefficients(gpu_ctx):
+    import paper_2110_10749_gb300 as ssd
+    clm = np.zeros(25)
+    clm[0] = 3.6      # |c_00| B_0 > 1
+    with pytest.raises(ssd.SsdError) as ei:
+        ssd.quadrature_points(gpu_ctx, ssd.STAR, h=1 / 8, clm=clm)
+    assert ei.value.status == ssd.SSD_EINVAL
+
+
+@pytest.mark.parametrize("seed", [5, -1])
+def test_star_jacobian_against_oracle_differences(gpu_ctx, seed):
+    """d(x, n, w)/dc_k against central differences of the oracle's point sets."""
+    import paper_2110_10749_gb300 as ssd
+    clm = _clm(seed)
+    h = 1 / 16
+    g = ssd.quadrature_points(gpu_ctx, ssd.STAR, h=h, clm=clm)
+    n = g["w"].numel()
+    J = {k: v.cpu().numpy() for k, v in ssd.quadrature_jacobian(gpu_ctx, clm, h, n).items()}
+    eps = 1e-6
+    for k in (0, 1, 5, 8, 12, 17, 20, 24):
+        cp, cm = clm.copy(), clm.copy()
+        cp[k] += eps
+        cm[k] -= eps
+        op, om = Q.star_points(cp, h), Q.star_points(cm, h)
+        assert np.array_equal(op["meta"], om["meta"]) and op["w"].size == n
+        for key, fk in (("xyz", "dxyz"), ("nrm", "dnrm"), ("w", "dw")):
+            fd = (op[key] - om[key]) / (2 * eps)
+            err = np.abs(J[fk][k] - fd).max()
+            assert err <= 1e-6 * np.abs(fd).max() + 1e-9, (k, key, err, np.abs(fd).max())
