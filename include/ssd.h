@@ -349,6 +349,42 @@ enum ssd_functional { SSD_FUNC_DRAG = 0, SSD_FUNC_FLUX = 1 };
 int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
                      int functional, double *value, double grad[2], ssd_stream stream);
 
+/*
+ * Geometric gradients.  For the scalar outputs of ssd_ddm_gradient, also the
+ * derivatives of J with respect to every point's data: gx[3][n] = dJ/dx_k,
+ * gn[3][n] = dJ/dn_k, gw[n] = dJ/dw_k (device, overwritten), with the point
+ * data treated as independent inputs of the discrete solve.  BJS traction
+ * only.  Contract them with ssd_quadrature_jacobian's outputs
+ * (ssd_shape_contract) for derivatives in shape coefficients.  Costs one more
+ * transposed Darcy solve, one Darcy solve and four FP64 pair passes of the
+ * geometric kernels below.  Synchronises `stream`.
+ */
+int ssd_ddm_gradient_geometry(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
+                              int functional, double *value, double grad[2], double *gx,
+                              double *gn, double *gw, ssd_stream stream);
+
+/*
+ * Derivatives of the bilinear form B(a, b) = sum_i a_i . (K b)_i in the point
+ * data, K the pair sum of op (SSD_OP_LAPLACE_SL, _DL, SSD_OP_STOKES_SL, _DL;
+ * Sections 5.1-5.3, double layers with their subtraction, single layers with
+ * their self term): adds alpha dB/dx_k to gx[3][n], alpha dB/dn_k to gn[3][n]
+ * and alpha dB/dw_k to gw[n] (device, accumulated).  a and b are [c][n]
+ * (c = 1 Laplace, 3 Stokes).  FP64, derivatives of the smoothed kernels in
+ * closed form (Taylor series below rho = 0.5).  Asynchronous on `stream`.
+ */
+int ssd_geometry_gradient(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu,
+                          double alpha, const double *a, const double *b, double *gx, double *gn,
+                          double *gw, ssd_stream stream);
+
+/*
+ * out[k] = sum_i dxyz[k][.][i] . gx[.][i] + dnrm[k][.][i] . gn[.][i] + dw[k][i] gw[i]
+ * for k < ncoef (1..512): the chain rule from point data to shape
+ * coefficients.  Device inputs, host output.  Synchronises `stream`.
+ */
+int ssd_shape_contract(ssd_ctx *ctx, int64_t n, int ncoef, const double *dxyz, const double *dnrm,
+                       const double *dw, const double *gx, const double *gn, const double *gw,
+                       double *out, ssd_stream stream);
+
 /* ------------------------------------------------------------------ batches
  * Many independent surfaces (uneven point counts, one smoothing radius each)
  * handled in one launch per operator application.  The caller concatenates

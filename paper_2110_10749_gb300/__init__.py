@@ -37,6 +37,7 @@ EXPORTS = [
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
+    "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 FUNC_DRAG, FUNC_FLUX = 0, 1
@@ -138,6 +139,10 @@ def lib():
         "ssd_stokes_DL_noalloc": [P, C.POINTER(CPoints), d, P, P, P],
         "ssd_apply_transpose": [P, C.POINTER(CPoints), i, d, d, P, P, i, P],
         "ssd_ddm_gradient": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(d), C.POINTER(d), P],
+        "ssd_ddm_gradient_geometry": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(d),
+                                      C.POINTER(d), P, P, P, P],
+        "ssd_geometry_gradient": [P, C.POINTER(CPoints), i, d, d, d, P, P, P, P, P, P],
+        "ssd_shape_contract": [P, i64, i, P, P, P, P, P, P, C.POINTER(d), P],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
         "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
@@ -457,7 +462,89 @@ def ddm_gradient(ctx, pts, prm, functional=FUNC_DRAG, raise_on_notconv=True):
     return val.value, np.array(g[:]), st
 
 
+def geometry_gradient(ctx, pts, op, delta, a, b, mu=1.0, alpha=1.0, out=None):
+    """Adds alpha d(a . K b)/d(x, n, w) to out = (gx, gn, gw) (allocated as zeros if None)."""
+    torch = _torch()
+    n = pts.n
+    if out is None:
+        dev = pts.xyz.device
+        out = (torch.zeros((3, n), dtype=torch.float64, device=dev), torch.zeros((3, n), dtype=torch.float64,
+               device=dev), torch.zeros((n,), dtype=torch.float64, device=dev))
+    ctx.check(lib().ssd_geometry_gradient(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu), float(alpha),
+                                          _ptr(a), _ptr(b), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream()),
+              "ssd_geometry_gradient")
+    return out
+
+
+def ddm_gradient_geometry(ctx, pts, prm, functional=FUNC_DRAG, raise_on_notconv=True):
+    """J, (dJ/dlog(kappa), dJ/dgamma) and dJ/d(x, n, w) per point."""
+    torch = _torch()
+    n = pts.n
+    dev = pts.xyz.device
+    gx = torch.empty((3, n), dtype=torch.float64, device=dev)
+    gn = torch.empty((3, n), dtype=torch.float64, device=dev)
+    gw = torch.empty((n,), dtype=torch.float64, device=dev)
+    val = C.c_double()
+    g = (C.c_double * 2)()
+    st = lib().ssd_ddm_gradient_geometry(ctx.h, C.byref(pts.c), C.byref(prm), int(functional), C.byref(val), g,
+                                         _ptr(gx), _ptr(gn), _ptr(gw), _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_ddm_gradient_geometry")
+    return val.value, np.array(g[:]), (gx, gn, gw), st
+
+
+def shape_contract(ctx, jac, geo):
+    """dJ/dc_k from a quadrature Jacobian (dict) and geometry gradients (gx, gn, gw)."""
+    ncoef, _, n = jac["dxyz"].shape
+    out = (C.c_double * ncoef)()
+    ctx.check(lib().ssd_shape_contract(ctx.h, int(n), int(ncoef), _ptr(jac["dxyz"]), _ptr(jac["dnrm"]),
+                                       _ptr(jac["dw"]), _ptr(geo[0]), _ptr(geo[1]), _ptr(geo[2]), out, _stream()),
+              "ssd_shape_contract")
+    return np.array(out[:])
+
+
+def ddm_shape_gradient(ctx, clm, h, prm, functional=FUNC_DRAG, angle_deg=70.0, center=(0.0, 0.0, 0.0)):
+    """On the STAR surface with coefficients clm at spacing h (delta taken from
+    prm): J, (dJ/dlog(kappa), dJ/dgamma) and dJ/dc_k for the 25 c_k."""
+    q = quadrature_points(ctx, STAR, h=h, angle_deg=angle_deg, center=center, clm=clm)
+    P = Points(q["xyz"], q["nrm"], q["w"]).prepare(ctx)
+    try:
+        J, g, geo, st = ddm_gradient_geometry(ctx, P, prm, functional)
+        jac = quadrature_jacobian(ctx, clm, h, P.n, angle_deg, center)
+        dc = shape_contract(ctx, jac, geo)
+    finally:
+        P.release()
+    return J, g, dc, st
+
+
 _DdmFunction = None
+_ShapeFunction = None
+
+
+def ddm_shape_functional(ctx, clm, h, prm, log_kappa, gamma, functional=FUNC_DRAG):
+    """Differentiable J(log(kappa), gamma, c_lm) on a STAR surface (torch.autograd);
+    clm is a (25,) float64 tensor."""
+    global _ShapeFunction
+    torch = _torch()
+    if _ShapeFunction is None:
+        class ShapeFunction(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, lk, gm, cl, c, h_, prm_, func):
+                p2 = CDdmParams.from_buffer_copy(prm_)
+                p2.kappa = float(np.exp(float(lk)))
+                p2.gamma = float(gm)
+                J, g, dc, _ = ddm_shape_gradient(c, cl.detach().cpu().numpy(), h_, p2, func)
+                dev = lk.device
+                fctx.save_for_backward(torch.tensor(g, dtype=torch.float64, device=dev),
+                                       torch.tensor(dc, dtype=torch.float64, device=cl.device))
+                return torch.tensor(J, dtype=torch.float64, device=dev)
+
+            @staticmethod
+            def backward(fctx, gout):
+                g, dc = fctx.saved_tensors
+                return gout * g[0], gout * g[1], gout * dc, None, None, None, None
+        _ShapeFunction = ShapeFunction
+    return _ShapeFunction.apply(log_kappa, gamma, clm, ctx, h, prm, functional)
 
 
 def ddm_functional(ctx, pts, prm, log_kappa, gamma, functional=FUNC_DRAG):

@@ -183,6 +183,8 @@ int pair_apply_batch(ssd_ctx *ctx, const BatchLayout &B, const BatchCall &bc, cu
 // Quadrature (quad.cu)
 int quadrature_points(ssd_ctx *ctx, const ssd_surface *surf, double h, double angle_deg, int64_t capacity,
                       int64_t *n_out, double *xyz, double *nrm, double *w, int32_t *meta, cudaStream_t s);
+int geometry_gradient(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu, double alpha,
+                      const double *a, const double *b, double *gx, double *gn, double *gw, cudaStream_t s);
 int quadrature_jacobian(ssd_ctx *ctx, const ssd_surface *surf, double h, double angle_deg, int64_t n, double *dxyz,
                         double *dnrm, double *dw, cudaStream_t s);
 

@@ -386,7 +386,8 @@ int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
 
 // ------------------------------------------------------------- local solves
 int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu, double kappa,
-                     const double *q, double *p, const ssd_krylov &kr, GmresResult *res, cudaStream_t s) {
+                     const double *q, double *p, const ssd_krylov &kr, GmresResult *res, cudaStream_t s,
+                     bool gauge = true) {
     const int64_t n = pts->n;
     Buf b, scal;
     SSD_TRY(b.alloc(ctx, sizeof(double) * n));
@@ -424,6 +425,7 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
         st = gmres(ctx, s, n, A, b.d(), p, kr.tol, kr.restart, kr.maxit, false, res);
     }
     if (st != SSD_OK && st != SSD_ENOTCONV) return st;
+    if (!gauge) return st;
     // zero weighted mean
     Dots dots;
     SSD_TRY(dots.init(ctx, s, 1));
@@ -847,14 +849,66 @@ struct Adjoint {
     }
 };
 
+// Pointwise geometric terms of the adjoint (derivatives in n_k, w_k, x_k of
+// the terms that are not pair sums).  Scalars: W = sum w, S1 = sum nu . n,
+// S2 = sum w n . u, S3 = sum (M^T nu) . n, sa = sum alpha, sg = sum g_p.
+struct GeoPoint {
+    int64_t n;
+    const double *xyz, *nrm, *w, *u, *p, *q, *lam, *nu, *mtnu;
+    double c, W, S1, S2, S3, sa, sg, e[3];
+    int deflate, functional;
+    double *gx, *gn, *gw;
+};
+__global__ void geo_point_kernel(const GeoPoint a) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = a.n;
+        double nk[3], uk[3], vk[3], nu[3];
+        for (int e = 0; e < 3; ++e) {
+            nk[e] = a.nrm[e * n + k]; uk[e] = a.u[e * n + k]; vk[e] = a.mtnu[e * n + k]; nu[e] = a.nu[e * n + k];
+        }
+        const double wk = a.w[k], pk = a.p[k];
+        const double vn = vk[0] * nk[0] + vk[1] * nk[1] + vk[2] * nk[2];
+        const double un = uk[0] * nk[0] + uk[1] * nk[1] + uk[2] * nk[2];
+        const double en = a.e[0] * nk[0] + a.e[1] * nk[1] + a.e[2] * nk[2];
+        double gn[3], gx[3] = {0, 0, 0};
+        // interface q = n . u, Stokes source M(n p), slip -c M(P u)
+        for (int e = 0; e < 3; ++e) gn[e] = a.lam[k] * uk[e] + pk * vk[e] + a.c * (vn * uk[e] + un * vk[e]);
+        // gauge projections of p in M(n p) and in -A_D's rank-one term
+        double gw = -pk * (a.S3 + a.sa) / a.W;
+        if (a.deflate) {
+            for (int e = 0; e < 3; ++e) gn[e] -= (nu[e] * a.S2 + a.S1 * wk * uk[e]) / a.W;
+            gw -= a.S1 * (un - a.S2 / a.W) / a.W;
+        }
+        if (a.functional == SSD_FUNC_DRAG) {
+            // J = sum_k w_k f_k . e, f = -p n + c (u - (u.n) n)
+            const double ue = uk[0] * a.e[0] + uk[1] * a.e[1] + uk[2] * a.e[2];
+            gw += -pk * en + a.c * (ue - un * en) - pk * a.sg / a.W;
+            for (int e = 0; e < 3; ++e) gn[e] += -wk * pk * a.e[e] - a.c * wk * (en * uk[e] + un * a.e[e]);
+        } else {
+            // J = sum_k w_k q_k (e . x_k)
+            const double ex = a.e[0] * a.xyz[k] + a.e[1] * a.xyz[n + k] + a.e[2] * a.xyz[2 * n + k];
+            gw += a.q[k] * ex;
+            for (int e = 0; e < 3; ++e) gx[e] += wk * a.q[k] * a.e[e];
+        }
+        for (int e = 0; e < 3; ++e) {
+            a.gx[e * n + k] = gx[e];
+            a.gn[e * n + k] = gn[e];
+        }
+        a.gw[k] = gw;
+    }
+}
+
 int ddm_gradient_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional, double *value,
-                      double grad[2], cudaStream_t s) {
+                      double grad[2], double *geo_x, double *geo_n, double *geo_w, cudaStream_t s) {
     SSD_TRY(check_ddm(ctx, prm));
     if (!prm->outer_gmres) return set_error(ctx, SSD_EINVAL, "gradients need the interface GMRES (outer_gmres = 1)");
     const bool jt = prm->traction_mode == SSD_TRACTION_JOSEPH_TAO;
     const bool implicit = prm->traction_mode == SSD_TRACTION_BJS && prm->bjs_implicit;
     if (!jt && !implicit && prm->gamma != 0.0)
         return set_error(ctx, SSD_EINVAL, "gradients need bjs_implicit = 1 in BJS mode with gamma != 0");
+    const bool geo = geo_x || geo_n || geo_w;
+    if (geo && !(geo_x && geo_n && geo_w)) return set_error(ctx, SSD_EINVAL, "geometry outputs must all be given");
+    if (geo && jt) return set_error(ctx, SSD_EINVAL, "geometry gradients need the BJS traction");
     if (functional != SSD_FUNC_DRAG && functional != SSD_FUNC_FLUX)
         return set_error(ctx, SSD_EINVAL, "unknown functional");
     if (prm->inner.use_sa) return set_error(ctx, SSD_EINVAL, "gradients need GMRES local solves (use_sa = 0)");
@@ -976,6 +1030,69 @@ int ddm_gradient_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params 
     }
     SSD_TRY(A.hdot(nu.d(), X0.d(), 3 * n, &h)); g0 += h;
     SSD_TRY(A.hdot(nu.d(), X1.d(), 3 * n, &h)); g1 += h;
+    if (geo) {
+        // alpha = A_D^{-T} P_g^T (g_p + N^T M^T nu), p~ = the Darcy solution before its gauge projection
+        Buf mtnu, al, pt, gp2, b3, t1;
+        SSD_TRY(t1.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(mtnu.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(al.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(pt.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(gp2.alloc(ctx, sizeof(double) * n));
+        SSD_TRY(b3.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(A.apply(OP_SSL, true, nu.d(), mtnu.d()));
+        dot_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, mtnu.d(), pts->nrm, gp2.d());
+        ctx->launches++;
+        double sg = 0.0;
+        if (functional == SSD_FUNC_DRAG) {
+            weight_field_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->xyz, pts->nrm, e0, e1, e2, 1, t1.d());
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, t1.d(), 1.0, gp2.d());
+            ctx->launches += 2;
+            SSD_TRY(A.sum(t1.d(), A.scal.d() + 6));
+            SSD_TRY(read_scalars(ctx, A.scal.d() + 6, 1, &sg, s));
+        }
+        double S3 = 0.0;
+        SSD_TRY(A.hdot(mtnu.d(), pts->nrm, 3 * n, &S3));
+        SSD_TRY(A.PgT(gp2.d()));
+        SSD_TRY(A.solveAdT(gp2.d(), al.d()));
+        GmresResult rd;
+        int sd = darcy_solve_impl(ctx, pts, *lref.L, prm->delta, prm->mu, prm->kappa, q.d(), pt.d(), prm->inner, &rd,
+                                  s, false);
+        if (sd == SSD_ENOTCONV) A.nonconv++;
+        else SSD_TRY(sd);
+        double sa = 0.0, S1 = 0.0, S2 = 0.0;
+        SSD_TRY(A.sum(al.d(), A.scal.d() + 6));
+        SSD_TRY(read_scalars(ctx, A.scal.d() + 6, 1, &sa, s));
+        SSD_TRY(A.hdot(nu.d(), pts->nrm, 3 * n, &S1));
+        scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, pts->w, pts->nrm, t3.d());
+        ctx->launches++;
+        SSD_TRY(A.hdot(t3.d(), u.d(), 3 * n, &S2));
+        GeoPoint gpk;
+        gpk.n = n; gpk.xyz = pts->xyz; gpk.nrm = pts->nrm; gpk.w = pts->w; gpk.u = u.d(); gpk.p = p.d();
+        gpk.q = q.d(); gpk.lam = lam.d(); gpk.nu = nu.d(); gpk.mtnu = mtnu.d();
+        gpk.c = A.c; gpk.W = lref.L->wsum; gpk.S1 = S1; gpk.S2 = S2; gpk.S3 = S3; gpk.sa = sa; gpk.sg = sg;
+        gpk.e[0] = e0; gpk.e[1] = e1; gpk.e[2] = e2;
+        gpk.deflate = prm->inner.deflate; gpk.functional = functional;
+        gpk.gx = geo_x; gpk.gn = geo_n; gpk.gw = geo_w;
+        geo_point_kernel<<<grid_for(n), 256, 0, s>>>(gpk);
+        ctx->launches++;
+        SSD_TRY(launch_check(ctx, "geometry point terms"));
+        // pair terms: (mu/kappa) B_L(alpha, q) + B_DL(alpha, p~) + B_M(nu, n p - c P u) + B_DS(nu, u)
+        SSD_TRY(geometry_gradient(ctx, pts, OP_LSL, prm->delta, prm->mu, prm->mu / prm->kappa, al.d(), q.d(), geo_x,
+                                  geo_n, geo_w, s));
+        SSD_TRY(geometry_gradient(ctx, pts, OP_LDL, prm->delta, prm->mu, 1.0, al.d(), pt.d(), geo_x, geo_n, geo_w,
+                                  s));
+        scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, p.d(), pts->nrm, b3.d());
+        ctx->launches++;
+        if (A.c != 0.0) {
+            axpby_kernel<<<grid_for(3 * n), 256, 0, s>>>(3 * n, -A.c, pu.d(), 1.0, b3.d());
+            ctx->launches++;
+        }
+        SSD_TRY(geometry_gradient(ctx, pts, OP_SSL, prm->delta, prm->mu, 1.0, nu.d(), b3.d(), geo_x, geo_n, geo_w,
+                                  s));
+        SSD_TRY(geometry_gradient(ctx, pts, OP_SDL, prm->delta, prm->mu, 1.0, nu.d(), u.d(), geo_x, geo_n, geo_w,
+                                  s));
+        SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "geometry sync"));
+    }
     if (value) *value = val;
     grad[0] = g0;
     grad[1] = g1;
@@ -1128,7 +1245,56 @@ int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     if (!grad) return set_error(ctx, SSD_EINVAL, "grad is NULL");
-    return ddm_gradient_impl(ctx, pts, prm, functional, value, grad, (cudaStream_t)stream);
+    return ddm_gradient_impl(ctx, pts, prm, functional, value, grad, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int ssd_ddm_gradient_geometry(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional,
+                              double *value, double grad[2], double *gx, double *gn, double *gw, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!grad) return set_error(ctx, SSD_EINVAL, "grad is NULL");
+    if (!gx || !gn || !gw) return set_error(ctx, SSD_EINVAL, "geometry outputs are NULL");
+    return ddm_gradient_impl(ctx, pts, prm, functional, value, grad, gx, gn, gw, (cudaStream_t)stream);
+}
+
+int ssd_geometry_gradient(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu, double alpha,
+                          const double *a, const double *b, double *gx, double *gn, double *gw, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    SSD_TRY(check_points(ctx, pts));
+    if (!(delta > 0.0) || !isfinite(delta) || !(mu > 0.0) || !isfinite(mu) || !isfinite(alpha))
+        return set_error(ctx, SSD_EINVAL, "delta and mu must be positive, alpha finite");
+    if (!a || !b || !gx || !gn || !gw) return set_error(ctx, SSD_EINVAL, "NULL array");
+    int iop;
+    switch (op) {
+        case SSD_OP_LAPLACE_SL: iop = OP_LSL; break;
+        case SSD_OP_LAPLACE_DL: iop = OP_LDL; break;
+        case SSD_OP_STOKES_SL: iop = OP_SSL; break;
+        case SSD_OP_STOKES_DL: iop = OP_SDL; break;
+        default: return set_error(ctx, SSD_EINVAL, "op must be a single or double layer");
+    }
+    return geometry_gradient(ctx, pts, iop, delta, mu, alpha, a, b, gx, gn, gw, (cudaStream_t)stream);
+}
+
+int ssd_shape_contract(ssd_ctx *ctx, int64_t n, int ncoef, const double *dxyz, const double *dnrm, const double *dw,
+                       const double *gx, const double *gn, const double *gw, double *out, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (n < 1 || ncoef < 1 || ncoef > 512) return set_error(ctx, SSD_EINVAL, "n >= 1 and 1 <= ncoef <= 512");
+    if (!dxyz || !dnrm || !dw || !gx || !gn || !gw || !out) return set_error(ctx, SSD_EINVAL, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, ncoef));
+    Buf r;
+    SSD_TRY(r.alloc(ctx, sizeof(double) * 3 * ncoef));
+    SSD_TRY(dots.multi(dxyz, 3 * n, ncoef, gx, 3 * n, r.d()));
+    SSD_TRY(dots.multi(dnrm, 3 * n, ncoef, gn, 3 * n, r.d() + ncoef));
+    SSD_TRY(dots.multi(dw, n, ncoef, gw, n, r.d() + 2 * ncoef));
+    std::vector<double> h(3 * (size_t)ncoef);
+    for (int part = 0; part < 3; ++part)
+        SSD_TRY(read_scalars(ctx, r.d() + part * ncoef, ncoef, h.data() + part * ncoef, s));
+    for (int k = 0; k < ncoef; ++k) out[k] = (h[k] + h[ncoef + k]) + h[2 * ncoef + k];
+    return SSD_OK;
 }
 
 int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double *nrm, const double *w,
