@@ -466,6 +466,7 @@ int check_points(ssd_ctx *ctx, const ssd_points *pts) {
 
 void release_layout(ssd_ctx *ctx, Layout *L) {
     if (L->block) dev_free(ctx, L->block);
+    if (L->order32) dev_free(ctx, L->order32);
     *L = Layout();
 }
 
@@ -599,6 +600,8 @@ int ssd_ctx_create(ssd_ctx **out, int device) {
         const int v = atoi(w);
         if (v >= 1 && v <= 64) ctx->waves32 = v;
     }
+    // tuning knob: 0 launches the FP32C grid in plain (tile, split) order
+    if (const char *w = getenv("SSD_PAIR_LPT")) ctx->lpt = atoi(w) != 0;
     *out = ctx;
     return SSD_OK;
 }
@@ -658,6 +661,7 @@ int ssd_points_prepare(ssd_ctx *ctx, ssd_points *pts, ssd_stream stream) {
     SSD_TRY(check_points(ctx, pts));
     ssd_layout *lay = new ssd_layout();
     int st = build_layout(ctx, pts, true, &lay->L, (cudaStream_t)stream);
+    lay->L.order_ok = true;
     if (st != SSD_OK) { delete lay; return st; }
     pts->layout = lay;
     return SSD_OK;

@@ -21,7 +21,10 @@ constexpr int kTile = 128;          // sources staged in shared memory per step
 #endif
 constexpr int kTPB32 = SSD_TPB32;         // threads per CTA, FP32C pair kernel
 constexpr int kMinCTA32 = SSD_MINCTA32;   // resident CTAs per SM the FP32C kernel is compiled for
-constexpr int kTPT32 = 4;           // targets per thread, FP32C (two packed f32x2 pairs)
+#ifndef SSD_TPT32
+#define SSD_TPT32 4
+#endif
+constexpr int kTPT32 = SSD_TPT32;   // targets per thread, FP32C (pairs of packed f32x2 lanes)
 constexpr int kChunk = 32;          // sources per bounding-box chunk (near/far test per warp)
 constexpr int kTPB64 = 128;         // threads per CTA, FP64 pair kernel
 constexpr int kTPT64 = 1;           // targets per thread, FP64
@@ -47,6 +50,12 @@ struct Layout {
     float4 *cbox = nullptr;    // per 32-point chunk: [2 * c] = (lo x, y, z, 0), [2 * c + 1] = (hi ...)
     double wsum = 0.0;         // sum of weights (host copy)
     void *block = nullptr;     // single allocation backing the arrays
+    // launch order of the FP32C pair grid (prepared layouts only), cached for
+    // the last (grid, rho_far delta) it was built for
+    bool order_ok = false;
+    int2 *order32 = nullptr;
+    int64_t order_nit = 0, order_chunk = 0;
+    float order_rfar2 = -1.f;
 };
 
 struct TimedLaunch {
@@ -66,6 +75,7 @@ struct ssd_ctx {
     int num_sms = 0;
     int occ32 = 1, occ64 = 1;  // resident CTAs per SM of the pair kernels
     int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
+    int lpt = 1;               // FP32C grid in near-first order on prepared layouts
     std::string err;
     // caching device allocator: blocks are reused in stream order
     struct Block { void *p; size_t bytes; bool used; };

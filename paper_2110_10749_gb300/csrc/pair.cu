@@ -359,6 +359,10 @@ struct K32Args {
     const BSurf *surfs;
     const Consts<float> *consts;
     int64_t rec_stride, part_stride;
+    // single-surface mode: optional launch order (blockIdx.x -> (target tile,
+    // split)), and 1 partial slot per target when every CTA holds one tile
+    const int2 *order = nullptr;
+    int nslot = 2;
 };
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
@@ -468,13 +472,19 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
         part_base = blockIdx.y * a.part_stride + NC * 2 * sf.pbase + (int64_t)it.split * NC * 2 * sf.n_pad - sf.poff;
         pstride = sf.n_pad;
     } else {
-        tbase = (int64_t)blockIdx.x * (kTPB32 * kTPT32);
-        s_beg = (int64_t)blockIdx.y * a.chunk;
+        int64_t bt = blockIdx.x, bs = blockIdx.y;
+        if (a.order) {
+            const int2 o = a.order[blockIdx.x];
+            bt = o.x;
+            bs = o.y;
+        }
+        tbase = bt * (kTPB32 * kTPT32);
+        s_beg = bs * a.chunk;
         s_end = s_beg + a.chunk;
         if (s_end > a.n_pad) s_end = a.n_pad;
         nreal_end = a.n;
         c = a.c;
-        part_base = (int64_t)blockIdx.y * NC * 2 * a.n_pad;
+        part_base = bs * NC * a.nslot * a.n_pad;
         pstride = a.n_pad;
     }
     // target t = 2k + j (pair k, lane j) is index tbase + threadIdx.x + t * kTPB32
@@ -622,9 +632,9 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
         const int64_t i = tbase + threadIdx.x + t * kTPB32;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            float *dst = a.part + part_base + (int64_t)(q * 2) * pstride + i;
+            float *dst = a.part + part_base + (int64_t)(q * a.nslot) * pstride + i;
             dst[0] = hi[t][q];
-            dst[pstride] = lo[t][q];
+            if (a.nslot == 2) dst[pstride] = lo[t][q];
         }
     }
 }
@@ -972,6 +982,82 @@ __global__ void bepilogue_kernel(const BEpiArgs a) {
 
 }  // namespace
 
+// Launch order of the single-surface FP32C grid: items (target tile, split)
+// with more near (warp, 32-source chunk) pairs first, so that the cheap far
+// items fill the last wave (longest-processing-time-first).  key = number of
+// near (warp, chunk) pairs of the item.
+__global__ void item_cost_kernel(const float4 *cbox, int64_t ntiles_t, int64_t nsplit, int64_t chunk, int64_t n_pad,
+                                 float rfar2, int32_t *key) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= ntiles_t * nsplit) return;
+    const int64_t t = it % ntiles_t, sp = it / ntiles_t;
+    constexpr int kWarps = kTPB32 / 32;
+    const int64_t c0 = t * (kTPB32 * kTPT32 / kChunk);
+    int cnt = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+        for (int k = 0; k < kTPT32; ++k) {
+            const int64_t cc = c0 + w + k * kWarps;
+            const float4 l = cbox[2 * cc], h = cbox[2 * cc + 1];
+            lo[0] = fminf(lo[0], l.x); lo[1] = fminf(lo[1], l.y); lo[2] = fminf(lo[2], l.z);
+            hi[0] = fmaxf(hi[0], h.x); hi[1] = fmaxf(hi[1], h.y); hi[2] = fmaxf(hi[2], h.z);
+        }
+        if (lo[0] > hi[0]) continue;
+        int64_t send = (sp + 1) * chunk;
+        if (send > n_pad) send = n_pad;
+        for (int64_t sc = sp * chunk / kChunk; sc < send / kChunk; ++sc) {
+            const float4 l = cbox[2 * sc], h = cbox[2 * sc + 1];
+            const float gx = fmaxf(0.f, fmaxf(l.x - hi[0], lo[0] - h.x));
+            const float gy = fmaxf(0.f, fmaxf(l.y - hi[1], lo[1] - h.y));
+            const float gz = fmaxf(0.f, fmaxf(l.z - hi[2], lo[2] - h.z));
+            cnt += (gx * gx + gy * gy + gz * gz < rfar2) ? 1 : 0;
+        }
+    }
+    key[it] = cnt;
+}
+
+// Builds (once per layout, delta and grid) the launch order of the FP32C grid.
+int item_order(ssd_ctx *ctx, const Layout &L, int64_t ntiles_t, int64_t nsplit, int64_t chunk, float rfar2,
+               const int2 **order, cudaStream_t s) {
+    Layout &M = const_cast<Layout &>(L);
+    const int64_t nit = ntiles_t * nsplit;
+    if (M.order32 && M.order_nit == nit && M.order_chunk == chunk && M.order_rfar2 == rfar2) {
+        *order = M.order32;
+        return SSD_OK;
+    }
+    if (M.order32) { dev_free(ctx, M.order32); M.order32 = nullptr; }
+    void *keys = nullptr;
+    SSD_TRY(dev_alloc(ctx, sizeof(int32_t) * nit, &keys));
+    struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } release{ctx, keys};
+    item_cost_kernel<<<(unsigned)((nit + 255) / 256), 256, 0, s>>>(L.cbox, ntiles_t, nsplit, chunk, L.n_pad, rfar2,
+                                                                   static_cast<int32_t *>(keys));
+    ctx->launches++;
+    SSD_TRY(launch_check(ctx, "item cost kernel"));
+    std::vector<int32_t> hk(nit);
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(hk.data(), keys, sizeof(int32_t) * nit, cudaMemcpyDeviceToHost, s),
+                       "key copy"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "key sync"));
+    // stable counting sort, largest key first
+    int32_t kmax = 0;
+    for (int64_t i = 0; i < nit; ++i) kmax = hk[i] > kmax ? hk[i] : kmax;
+    std::vector<int64_t> start(kmax + 2, 0);
+    for (int64_t i = 0; i < nit; ++i) start[kmax - hk[i] + 1]++;
+    for (int k = 1; k <= kmax + 1; ++k) start[k] += start[k - 1];
+    std::vector<int2> ho(nit);
+    for (int64_t i = 0; i < nit; ++i) ho[start[kmax - hk[i]]++] = make_int2((int)(i % ntiles_t), (int)(i / ntiles_t));
+    void *dev = nullptr;
+    SSD_TRY(dev_alloc(ctx, sizeof(int2) * nit, &dev));
+    M.order32 = static_cast<int2 *>(dev);
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(M.order32, ho.data(), sizeof(int2) * nit, cudaMemcpyHostToDevice, s),
+                       "order copy"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "order sync"));
+    M.order_nit = nit;
+    M.order_chunk = chunk;
+    M.order_rfar2 = rfar2;
+    *order = M.order32;
+    return SSD_OK;
+}
+
 int pair_occupancy(ssd_ctx *ctx) {
     int o32 = 0, o64 = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, pair32_kernel<OP_SSLDL>, kTPB32, 0);
@@ -1007,7 +1093,9 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const int64_t chunk = chunk_tiles * kTile;
 
     const size_t rec = f32 ? sizeof(float4) : sizeof(d4);
-    const int nslot = f32 ? 2 : 1;
+    // FP32C keeps a (hi, lo) pair per target and split; one slot suffices when
+    // every CTA of the packed kernel holds a single source tile (lo stays 0)
+    const int nslot = f32 ? ((packed32 && chunk == kTile) ? 1 : 2) : 1;
     const size_t rsz = f32 ? sizeof(float) : sizeof(double);
     const bool two_rec = (op == OP_SSLDL);
     const int pack_blocks = (int)((n_pad + 255) / 256);
@@ -1083,7 +1171,16 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.c = make_consts<float>(pc.delta, kRhoFar32);
         ka.part = reinterpret_cast<float *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
-        e = launch_pair_op32(op, grid, ka, s);
+        ka.nslot = nslot;
+        dim3 g = grid;
+        if (ctx->lpt && L.order_ok) {
+            const int2 *ord = nullptr;
+            const int st = item_order(ctx, L, ntiles_t, nsplit, chunk, ka.c.rfar2, &ord, s);
+            if (st != SSD_OK) return st;
+            ka.order = ord;
+            g = dim3((unsigned)(ntiles_t * nsplit), 1);
+        }
+        e = launch_pair_op32(op, g, ka, s);
     } else {
         KArgs<double> ka;
         ka.pos = L.pos64; ka.wn = L.wn64;
