@@ -87,6 +87,25 @@ void timed_end(ssd_ctx *ctx, cudaStream_t s, cudaEvent_t beg, int cls, int prec,
     ctx->pending.push_back({beg, e, cls, prec == SSD_FP32C ? 1 : 0, pairs});
 }
 
+int frame_acquire(ssd_ctx *ctx, double **slots, cudaEvent_t ev[2]) {
+    if (ctx->hsp >= kHostFrames) return set_error(ctx, SSD_EINVAL, "GMRES nesting too deep");
+    const int f = ctx->hsp;
+    while ((int)ctx->sync_ev.size() < 2 * (f + 1)) {
+        cudaEvent_t e;
+        SSD_TRY(cuda_check(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create"));
+        ctx->sync_ev.push_back(e);
+    }
+    *slots = ctx->hbuf + 512 + 4 * f;
+    ev[0] = ctx->sync_ev[2 * f];
+    ev[1] = ctx->sync_ev[2 * f + 1];
+    ctx->hsp++;
+    return SSD_OK;
+}
+
+void frame_release(ssd_ctx *ctx) {
+    if (ctx->hsp > 0) ctx->hsp--;
+}
+
 static int drain_timing(ssd_ctx *ctx) {
     for (auto &t : ctx->pending) {
         float ms = 0.f;
@@ -593,7 +612,7 @@ int ssd_ctx_create(ssd_ctx **out, int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete ctx; return SSD_ECUDA; }
     ctx->num_sms = prop.multiProcessorCount;
-    if (cudaMallocHost((void **)&ctx->hbuf, 4096) != cudaSuccess) { delete ctx; return SSD_ENOMEM; }
+    if (cudaMallocHost((void **)&ctx->hbuf, 8192) != cudaSuccess) { delete ctx; return SSD_ENOMEM; }
     if (pair_occupancy(ctx) != SSD_OK) { cudaFreeHost(ctx->hbuf); delete ctx; return SSD_ECUDA; }
     // tuning knob: waves of resident CTAs in an FP32C pair-kernel grid
     if (const char *w = getenv("SSD_PAIR_WAVES")) {
@@ -613,6 +632,7 @@ int ssd_ctx_destroy(ssd_ctx *ctx) {
     for (auto &b : ctx->pool) cudaFree(b.p);
     for (auto &t : ctx->pending) { cudaEventDestroy(t.beg); cudaEventDestroy(t.end); }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto e : ctx->sync_ev) cudaEventDestroy(e);
     if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
     delete ctx;
     return SSD_OK;

@@ -81,7 +81,9 @@ struct ssd_ctx {
     struct Block { void *p; size_t bytes; bool used; };
     std::vector<Block> pool;
     // pinned host scratch for small device->host reads
-    double *hbuf = nullptr;
+    double *hbuf = nullptr;     // pinned: [0, 512) scalar reads, [512, 1024) GMRES frames
+    int hsp = 0;                // GMRES frames in use (nested solves take one each)
+    std::vector<cudaEvent_t> sync_ev;   // two per frame, created on first use
     // timing
     bool timing = false;
     std::vector<ssd::TimedLaunch> pending;
@@ -116,6 +118,13 @@ struct LayoutRef {
 };
 int get_layout(ssd_ctx *ctx, const ssd_points *pts, LayoutRef *ref, cudaStream_t s);
 int check_points(ssd_ctx *ctx, const ssd_points *pts);
+
+// Pinned frame of 4 doubles and two events for one GMRES solve, so that
+// its residual can be read back asynchronously while nested solves use their
+// own frames (LIFO).  (ctx.cu)
+constexpr int kHostFrames = 128;
+int frame_acquire(ssd_ctx *ctx, double **slots, cudaEvent_t ev[2]);
+void frame_release(ssd_ctx *ctx);
 
 // Timing (ctx.cu)
 int timed_begin(ssd_ctx *ctx, cudaStream_t s, cudaEvent_t *beg);

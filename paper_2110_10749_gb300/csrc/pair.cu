@@ -760,17 +760,49 @@ __global__ void epilogue_kernel(const EpiArgs a) {
     const int64_t i = g - (int64_t)q * a.n_pad;
     const int32_t o = a.perm[i];
     if (o < 0) return;
-    double s = 0.0;
-    for (int sp = 0; sp < a.nsplit; ++sp) {
-        const int64_t base = (((int64_t)sp * a.nc + q) * a.nslot) * a.n_pad + i;
-        if (a.part_is_float) {
-            const float *pf = reinterpret_cast<const float *>(a.part);
-            s += (double)pf[base];
-            if (a.nslot == 2) s += (double)pf[base + a.n_pad];
-        } else {
-            s += reinterpret_cast<const double *>(a.part)[base];
+    // four interleaved partial sums over the splits (loads stay in flight),
+    // combined in a fixed order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const int64_t sstride = (int64_t)a.nc * a.nslot * a.n_pad;
+    const int64_t base0 = ((int64_t)q * a.nslot) * a.n_pad + i;
+    if (a.part_is_float) {
+        // FP32 partials summed with an error-free transformation (TwoSum) into
+        // a (hi, lo) pair: FP32 arithmetic, no rounding error beyond lo's
+        // loads are issued eight splits ahead of the sums
+        const float *pf = reinterpret_cast<const float *>(a.part);
+        float hi = 0.f, lo = 0.f;
+        auto two_sum = [&](float p) {
+            const float t = hi + p;
+            const float bp = t - hi;
+            lo += (hi - (t - bp)) + (p - bp);
+            hi = t;
+        };
+        int sp = 0;
+        if (a.nslot == 1) {
+            for (; sp + 7 < a.nsplit; sp += 8) {
+                float p[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) p[u] = pf[base0 + (sp + u) * sstride];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) two_sum(p[u]);
+            }
         }
+        for (; sp < a.nsplit; ++sp)
+            for (int l = 0; l < a.nslot; ++l) two_sum(pf[base0 + sp * sstride + l * a.n_pad]);
+        s0 = (double)hi + (double)lo;
+    } else {
+        const double *pd = reinterpret_cast<const double *>(a.part);
+        int sp = 0;
+        for (; sp + 3 < a.nsplit; sp += 4) {
+            const int64_t b = base0 + sp * sstride;
+            s0 += pd[b];
+            s1 += pd[b + sstride];
+            s2 += pd[b + 2 * sstride];
+            s3 += pd[b + 3 * sstride];
+        }
+        for (; sp < a.nsplit; ++sp) s0 += pd[base0 + sp * sstride];
     }
+    const double s = (s0 + s1) + (s2 + s3);
     double v = a.scale * s * (a.weight_out ? a.pos64[i].w : 1.0);
     if (a.self_src) v += a.self_coef * a.pos64[i].w * a.self_src[(int64_t)q * a.n + o];
     double r = a.a_op * v + extra + (q == 0 ? a.add0 : (q == 1 ? a.add1 : a.add2));

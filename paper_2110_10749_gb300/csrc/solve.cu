@@ -15,49 +15,86 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------ vector kernels
-constexpr int kDotThreads = 256;
 constexpr int kMaxRestart = 256;
-constexpr int kDotMaxBlocks = 120;
+constexpr int kDotMaxBlocks = 512;
 
-// partial[v * nbx + bx] = sum over this block's chunk of V[v] . w
-__global__ void multidot_kernel(const double *V, int64_t ldv, const double *w, int64_t n, int64_t chunk,
-                                double *partial) {
-    __shared__ double red[kDotThreads];
-    const int v = blockIdx.y;
+// One warp per vector: partial[v * gridDim.x + bx] = V[v][rows of bx] . w
+// over the block's row chunk (lanes stride 32 rows, four accumulators,
+// shuffle reduction in a fixed pattern).  Blocks hold 8 warps = 8 vectors.
+__global__ void multidot_warp_kernel(const double *V, int64_t ldv, const double *w, int64_t n, int64_t chunk,
+                                     int nv, double *partial, const double *cond) {
+    const int lane = threadIdx.x & 31;
+    const int v = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (v >= nv) return;
+    double *dst = partial + (int64_t)v * gridDim.x + blockIdx.x;
+    if (cond && *cond == 0.0) {
+        if (lane == 0) *dst = 0.0;
+        return;
+    }
     const double *a = V + (int64_t)v * ldv;
     const int64_t beg = (int64_t)blockIdx.x * chunk;
     int64_t end = beg + chunk;
     if (end > n) end = n;
-    double s = 0.0;
-    for (int64_t k = beg + threadIdx.x; k < end; k += kDotThreads) s += a[k] * w[k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int st = kDotThreads / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
-        __syncthreads();
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t k = beg + lane;
+    for (; k + 96 < end; k += 128) {
+        s0 += a[k] * w[k];
+        s1 += a[k + 32] * w[k + 32];
+        s2 += a[k + 64] * w[k + 64];
+        s3 += a[k + 96] * w[k + 96];
     }
-    if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
+    for (; k < end; k += 32) s0 += a[k] * w[k];
+    double t = (s0 + s1) + (s2 + s3);
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) *dst = t;
 }
 
-__global__ void multidot_finish_kernel(const double *partial, int nbx, int nv, double *out) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+// out[v] = sum_b partial[v * nbx + b], one warp per vector
+__global__ void multidot_finish_warp_kernel(const double *partial, int nbx, int nv, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int v = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (v >= nv) return;
-    double s = 0.0;
-    for (int k = 0; k < nbx; ++k) s += partial[(int64_t)v * nbx + k];
-    out[v] = s;
+    double t = 0.0;
+    for (int b = lane; b < nbx; b += 32) t += partial[(int64_t)v * nbx + b];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) out[v] = t;
 }
 
-// w += sign * sum_v coef[v] V[v]
+// w += sign * sum_v coef[v] V[v] (skipped when cond is set and *cond == 0);
+// eight interleaved accumulators per row, combined in a fixed order
 __global__ void vupdate_kernel(const double *V, int64_t ldv, int nv, const double *coef, double sign, double *w,
-                               int64_t n) {
-    __shared__ double c[kMaxRestart + 2];
+                               int64_t n, const double *cond = nullptr) {
+    if (cond && *cond == 0.0) return;
+    __shared__ double c[kMaxRestart + 4];
     for (int v = threadIdx.x; v < nv; v += blockDim.x) c[v] = sign * coef[v];
     __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        double acc = w[k];
-        for (int v = 0; v < nv; ++v) acc += c[v] * V[(int64_t)v * ldv + k];
-        w[k] = acc;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int v = 0;
+        for (; v + 7 < nv; v += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] += c[v + u] * V[(int64_t)(v + u) * ldv + k];
+        }
+        for (; v < nv; ++v) a[0] += c[v] * V[(int64_t)v * ldv + k];
+        w[k] += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     }
+}
+
+// Reorthogonalisation test of Daniel, Gragg, Kaufman and Stewart: after the
+// first Gram-Schmidt pass h = V^T w (h[0..j]) with h[j+1] = w . w, the
+// remaining norm is ||w||^2 - sum h_i^2; a second pass runs when more than
+// half of ||w||^2 was removed.  Writes the decision to h[j+2] (1 or 0).
+__global__ void dgks_kernel(double *h, int j) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 256) s += h[i] * h[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) h[j + 2] = (red[0] > 0.5 * h[j + 1]) ? 1.0 : 0.0;
 }
 
 // y = a x + b y
@@ -81,43 +118,87 @@ __global__ void sub_dev_scalar_kernel(int64_t n, const double *s, double f, doub
         y[k] -= v;
 }
 
-// GMRES bookkeeping, one thread: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2),
-// previous rotations applied, new rotation formed, residual estimate updated.
+// GMRES bookkeeping: H(:, j) = h1 + h2, H(j+1, j) = sqrt(nrm2), previous
+// rotations applied, new rotation formed, residual estimate updated.
+// Applying rotations 0..j-1 to the new column is the affine recurrence
+// a_{i+1} = -s_i a_i + c_i b_i (a_0 = col_0, b_i = col_{i+1}), after which
+// col_i = c_i a_i + s_i b_i.  The recurrence is evaluated as an inclusive
+// scan of the affine maps (Hillis-Steele, fixed order), so the FP64
+// dependency chain is log2(j) steps long instead of j.  Block of 256 threads.
 __global__ void givens_kernel(double *H, int ldh, double *cs, double *sn, double *g, const double *h1,
                               const double *h2, const double *nrm2, int j, double *out) {
-    if (threadIdx.x != 0) return;
-    double *col = H + (int64_t)j * ldh;
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-    const double hn = sqrt(fmax(*nrm2, 0.0));
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
+    __shared__ double col[kMaxRestart + 2], al[2][kMaxRestart], be[2][kMaxRestart];
+    const int t = threadIdx.x;
+    for (int i = t; i <= j; i += blockDim.x) col[i] = h1[i] + h2[i];
+    __syncthreads();
+    double ci = 0.0, si = 0.0, bi = 0.0;
+    if (t < j) {
+        ci = cs[t];
+        si = sn[t];
+        bi = col[t + 1];
+        al[0][t] = -si;
+        be[0][t] = ci * bi;
     }
-    const double den = hypot(col[j], col[j + 1]);
-    if (den == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-    } else {
-        cs[j] = col[j] / den;
-        sn[j] = col[j + 1] / den;
+    __syncthreads();
+    int cur = 0;
+    for (int off = 1; off < j; off <<= 1) {
+        if (t < j) {
+            if (t >= off) {
+                const double a = al[cur][t], b = be[cur][t];
+                al[cur ^ 1][t] = a * al[cur][t - off];
+                be[cur ^ 1][t] = a * be[cur][t - off] + b;
+            } else {
+                al[cur ^ 1][t] = al[cur][t];
+                be[cur ^ 1][t] = be[cur][t];
+            }
+        }
+        cur ^= 1;
+        __syncthreads();
     }
-    col[j] = den;
-    col[j + 1] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    out[0] = fabs(g[j + 1]);
-    out[1] = hn;
+    const double a0 = col[0];
+    __syncthreads();
+    if (t < j) {
+        const double ai = t == 0 ? a0 : al[cur][t - 1] * a0 + be[cur][t - 1];
+        col[t] = ci * ai + si * bi;
+    }
+    if (t == 0 && j > 0) col[j] = al[cur][j - 1] * a0 + be[cur][j - 1];
+    __syncthreads();
+    double *hc = H + (int64_t)j * ldh;
+    if (t == 0) {
+        const double hn = sqrt(fmax(*nrm2, 0.0));
+        const double den = hypot(col[j], hn);
+        double cj = 1.0, sj = 0.0;
+        if (den != 0.0) {
+            cj = col[j] / den;
+            sj = hn / den;
+        }
+        cs[j] = cj;
+        sn[j] = sj;
+        col[j] = den;
+        col[j + 1] = 0.0;
+        const double gj = g[j];
+        g[j + 1] = -sj * gj;
+        g[j] = cj * gj;
+        out[0] = fabs(g[j + 1]);
+        out[1] = hn;
+    }
+    __syncthreads();
+    for (int i = t; i <= j + 1; i += blockDim.x) hc[i] = col[i];
 }
 
-// Back substitution H(0:k, 0:k) y = g(0:k), one thread.
+// Back substitution H(0:k, 0:k) y = g(0:k), column by column: y_i is fixed,
+// then every earlier right-hand side entry drops H(l, i) y_i in parallel.
 __global__ void backsolve_kernel(const double *H, int ldh, const double *g, int k, double *y) {
-    if (threadIdx.x != 0) return;
+    __shared__ double b[kMaxRestart];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) b[i] = g[i];
+    __syncthreads();
     for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int l = i + 1; l < k; ++l) s -= H[(int64_t)l * ldh + i] * y[l];
-        y[i] = s / H[(int64_t)i * ldh + i];
+        const double *hc = H + (int64_t)i * ldh;
+        const double yi = b[i] / hc[i];
+        __syncthreads();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) b[l] -= hc[l] * yi;
+        if (threadIdx.x == 0) y[i] = yi;
+        __syncthreads();
     }
 }
 
@@ -220,15 +301,17 @@ struct Dots {
         s = st;
         return partial.alloc(c, sizeof(double) * kDotMaxBlocks * (maxv + 1));
     }
-    // out[v] = V[v] . w, v < nv (deterministic)
-    int multi(const double *V, int64_t ldv, int nv, const double *w, int64_t n, double *out) {
-        int64_t nbx = (n + 4095) / 4096;
-        if (nbx > kDotMaxBlocks) nbx = kDotMaxBlocks;
-        if (nbx < 1) nbx = 1;
-        const int64_t chunk = (n + nbx - 1) / nbx;
-        multidot_kernel<<<dim3((unsigned)nbx, (unsigned)nv), kDotThreads, 0, s>>>(V, ldv, w, n, chunk,
-                                                                                  partial.d());
-        multidot_finish_kernel<<<(nv + 127) / 128, 128, 0, s>>>(partial.d(), (int)nbx, nv, out);
+    // out[v] = V[v] . w, v < nv (deterministic); out = 0 when cond && *cond == 0
+    int multi(const double *V, int64_t ldv, int nv, const double *w, int64_t n, double *out,
+              const double *cond = nullptr) {
+        // row chunks of at least 1024 (a multiple of 128), at most kDotMaxBlocks of them
+        int64_t chunk = (n + kDotMaxBlocks - 1) / kDotMaxBlocks;
+        if (chunk < 1024) chunk = 1024;
+        chunk = (chunk + 127) / 128 * 128;
+        const int64_t nbx = (n + chunk - 1) / chunk;
+        multidot_warp_kernel<<<dim3((unsigned)nbx, (unsigned)((nv + 7) / 8)), 256, 0, s>>>(V, ldv, w, n, chunk, nv,
+                                                                                          partial.d(), cond);
+        multidot_finish_warp_kernel<<<(nv + 7) / 8, 256, 0, s>>>(partial.d(), (int)nbx, nv, out);
         ctx->launches += 2;
         return launch_check(ctx, "dot kernels");
     }
@@ -250,23 +333,32 @@ struct GmresResult {
     double relres = 1.0;
 };
 
-// Restarted GMRES (Saad) with classical Gram-Schmidt and one
-// reorthogonalisation (CGS2), x0 = 0 unless `warm`.  Stops when the residual
+// Restarted GMRES (Saad) with classical Gram-Schmidt and a second
+// (re)orthogonalisation pass when the DGKS test calls for it, x0 = 0 unless
+// `warm`.  Stops when the residual
 // estimate falls to tol * ||b|| or after maxit Arnoldi steps.
 int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double *b, double *x, double tol,
-          int restart, int maxit, bool warm, GmresResult *res) {
+          int restart, int maxit, bool warm, GmresResult *res, bool pipeline = true) {
     const int m = restart;
-    Buf V, w, small;
+    // residual estimates come back through a pinned frame: with `pipeline`
+    // the next Arnoldi step is queued before the previous one's residual is
+    // read (while that residual is still above 30 tol), so the host never
+    // leaves the GPU idle between steps; a step queued past convergence is
+    // discarded
+    double *slot = nullptr;
+    cudaEvent_t ev[2];
+    SSD_TRY(frame_acquire(ctx, &slot, ev));
+    struct FrameGuard { ssd_ctx *c; ~FrameGuard() { frame_release(c); } } frame_guard{ctx};
+    Buf V, small;
     SSD_TRY(V.alloc(ctx, sizeof(double) * (size_t)(m + 1) * n));
-    SSD_TRY(w.alloc(ctx, sizeof(double) * n));
     const int ldh = m + 1;
-    // small: H[(m+1)*m], cs[m], sn[m], g[m+1], h1[m+1], h2[m+1], y[m], scal[8]
-    const size_t nsmall = (size_t)ldh * m + 2 * m + 3 * (m + 1) + m + 8;
+    // small: H[(m+1)*m], cs[m], sn[m], g[m+1], h1[m+3], h2[m+3], y[m], scal[8]
+    const size_t nsmall = (size_t)ldh * m + 2 * m + (m + 1) + 2 * (m + 3) + m + 8;
     SSD_TRY(small.alloc(ctx, sizeof(double) * nsmall));
     double *H = small.d(), *cs = H + (size_t)ldh * m, *sn = cs + m, *g = sn + m, *h1 = g + m + 1,
-           *h2 = h1 + m + 1, *y = h2 + m + 1, *scal = y + m;
+           *h2 = h1 + m + 3, *y = h2 + m + 3, *scal = y + m;
     Dots dots;
-    SSD_TRY(dots.init(ctx, s, m + 1));
+    SSD_TRY(dots.init(ctx, s, m + 2));
     const unsigned gb = grid_for(n);
 
     // ||b||
@@ -308,29 +400,65 @@ int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double
         if (rel <= tol || total >= maxit || hb[0] == 0.0) break;
         int k = 0;
         bool done = false;
+        double prev_rel = rel;
+        int pending = -1;      // queued step whose residual has not been read yet
+        auto fetch = [&](int step) -> int {
+            SSD_TRY(cuda_check(ctx, cudaEventSynchronize(ev[step & 1]), "event sync"));
+            hb[0] = slot[2 * (step & 1)];
+            hb[1] = slot[2 * (step & 1) + 1];
+            return SSD_OK;
+        };
         for (int j = 0; j < m; ++j) {
             double *vj = V.d() + (size_t)j * n;
-            SSD_TRY(A(vj, w.d()));
+            double *w = V.d() + (size_t)(j + 1) * n;    // the new vector is built in its slot
+            SSD_TRY(A(vj, w));
             ++total;
-            SSD_TRY(dots.multi(V.d(), n, j + 1, w.d(), n, h1));
-            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h1, -1.0, w.d(), n);
+            // Gram-Schmidt pass (h1[j+1] = w . w from the same sweep), the
+            // DGKS test, and a second pass only when the test asks for it
+            SSD_TRY(dots.multi(V.d(), n, j + 2, w, n, h1));
+            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h1, -1.0, w, n);
+            dgks_kernel<<<1, 256, 0, s>>>(h1, j);
+            ctx->launches += 2;
+            SSD_TRY(dots.multi(V.d(), n, j + 1, w, n, h2, h1 + j + 2));
+            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h2, -1.0, w, n, h1 + j + 2);
             ctx->launches++;
-            SSD_TRY(dots.multi(V.d(), n, j + 1, w.d(), n, h2));
-            vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h2, -1.0, w.d(), n);
-            ctx->launches++;
-            SSD_TRY(dots.multi(w.d(), 0, 1, w.d(), n, scal + 2));
-            givens_kernel<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, h1, h2, scal + 2, j, scal);
-            scale_inv_kernel<<<gb, 256, 0, s>>>(n, w.d(), scal + 1, V.d() + (size_t)(j + 1) * n);
+            SSD_TRY(dots.multi(w, 0, 1, w, n, scal + 2));
+            givens_kernel<<<1, 256, 0, s>>>(H, ldh, cs, sn, g, h1, h2, scal + 2, j, scal);
+            scale_inv_kernel<<<gb, 256, 0, s>>>(n, w, scal + 1, w);
             ctx->launches += 2;
             SSD_TRY(launch_check(ctx, "arnoldi step"));
-            SSD_TRY(read_scalars(ctx, scal, 2, hb, s));
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(slot + 2 * (j & 1), scal, 2 * sizeof(double),
+                                                    cudaMemcpyDeviceToHost, s), "residual copy"));
+            SSD_TRY(cuda_check(ctx, cudaEventRecord(ev[j & 1], s), "event record"));
+            if (pending >= 0) {
+                // step j was queued ahead: read step j - 1 now
+                SSD_TRY(fetch(pending));
+                rel = hb[0] / bnorm;
+                res->relres = rel;
+                if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
+                if (rel <= tol || hb[1] == 0.0) {
+                    k = pending + 1;      // discard step j
+                    --total;
+                    done = true;
+                    break;
+                }
+                prev_rel = rel;
+                pending = -1;
+            }
+            const bool last = (j + 1 >= m) || (total >= maxit);
+            if (pipeline && !last && prev_rel > 30.0 * tol) {
+                pending = j;
+                continue;
+            }
+            SSD_TRY(fetch(j));
             k = j + 1;
             rel = hb[0] / bnorm;
             res->relres = rel;
             if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
             if (rel <= tol || total >= maxit || hb[1] == 0.0) { done = true; break; }
+            prev_rel = rel;
         }
-        backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+        backsolve_kernel<<<1, 256, 0, s>>>(H, ldh, g, k, y);
         vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, k, y, 1.0, x, n);
         ctx->launches += 2;
         SSD_TRY(launch_check(ctx, "gmres update"));
@@ -630,7 +758,8 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
         };
         GmresResult gr;
         const int m_out = prm->maxit_outer < 128 ? prm->maxit_outer : 128;
-        int st = gmres(ctx, s, nz, F, c.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr);
+        // each matvec is a whole sweep: no step is queued ahead of its check
+        int st = gmres(ctx, s, nz, F, c.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr, false);
         if (st == SSD_ENOTCONV) status = SSD_ENOTCONV;
         else SSD_TRY(st);
         its = gr.iters;
@@ -1019,7 +1148,8 @@ int ddm_gradient_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params 
         GmresResult r;
         const int m = prm->maxit_outer < 128 ? prm->maxit_outer : 128;
         auto M = [&](const double *v, double *o) -> int { return A.interface_matvec(v, o); };
-        const int st = gmres(ctx, s, n, M, zeta.d(), lam.d(), prm->tol_outer, m, prm->maxit_outer, false, &r);
+        const int st = gmres(ctx, s, n, M, zeta.d(), lam.d(), prm->tol_outer, m, prm->maxit_outer, false, &r,
+                             false);
         if (st == SSD_ENOTCONV) A.nonconv++;
         else SSD_TRY(st);
         scal_normal_kernel<<<grid_for(n), 256, 0, s>>>(n, lam.d(), pts->nrm, t3.d());
