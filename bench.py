@@ -50,6 +50,7 @@ UNIT = "pair-interactions/s"
 FLOPS_SDL_FAR = 33
 FLOPS_SDL_NEAR = 50
 RHO_FAR = 5.5
+DRAM_BYTES_SSLDL = 1201152
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -304,8 +305,11 @@ def run_ours(args):
     sms = props.multi_processor_count
     peak = sms * 128 * 2 * 2070e6 / 1e12
     achieved = dom["pairs"] * flops_pair / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "pair_kernel<float,%s>" % names[dom_cls], "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    # DRAM bytes (read + write) per launch of the fused Stokes kernel on this
+    # workload, from one ncu capture (the sources stay in L2 between launches)
+    traffic = DRAM_BYTES_SSLDL if dom_cls == ssd.K_STOKES_SLDL else None
+    roofline = {"bound": "alu", "kernel": "pair32_kernel<%s> (FP32C, packed f32x2)" % names[dom_cls],
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "flops_per_pair": flops_pair, "near_fraction": fnear,
                 "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1),
                 "share_of_step": dom["ms"] / total_ms if total_ms > 0 else None,

@@ -238,7 +238,7 @@ typedef struct {
     double tol;    /* stop when ||b - A x|| <= tol ||b|| (GMRES estimate) or, for SA,
                       when ||x_k - x_{k-1}|| <= tol ||x_k|| */
     int maxit;     /* total iteration limit */
-    int restart;   /* GMRES restart length m (1..256) */
+    int restart;   /* GMRES restart length m (1..512; batched solves 1..256) */
     int use_sa;    /* 1: successive approximations (eqs. Darcy_BIEM_iter,
                       Stokes_BIEM_iter) instead of GMRES */
     int prec;      /* enum ssd_precision of the pair sums */

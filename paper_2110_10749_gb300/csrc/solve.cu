@@ -15,7 +15,7 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------ vector kernels
-constexpr int kMaxRestart = 256;
+constexpr int kMaxRestart = 512;
 constexpr int kDotMaxBlocks = 512;
 
 // One warp per vector: partial[v * gridDim.x + bx] = V[v][rows of bx] . w
@@ -124,7 +124,8 @@ __global__ void sub_dev_scalar_kernel(int64_t n, const double *s, double f, doub
 // a_{i+1} = -s_i a_i + c_i b_i (a_0 = col_0, b_i = col_{i+1}), after which
 // col_i = c_i a_i + s_i b_i.  The recurrence is evaluated as an inclusive
 // scan of the affine maps (Hillis-Steele, fixed order), so the FP64
-// dependency chain is log2(j) steps long instead of j.  Block of 256 threads.
+// dependency chain is log2(j) steps long instead of j.  Block of kMaxRestart
+// threads (one per rotation).
 __global__ void givens_kernel(double *H, int ldh, double *cs, double *sn, double *g, const double *h1,
                               const double *h2, const double *nrm2, int j, double *out) {
     __shared__ double col[kMaxRestart + 2], al[2][kMaxRestart], be[2][kMaxRestart];
@@ -423,7 +424,7 @@ int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double
             vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h2, -1.0, w, n, h1 + j + 2);
             ctx->launches++;
             SSD_TRY(dots.multi(w, 0, 1, w, n, scal + 2));
-            givens_kernel<<<1, 256, 0, s>>>(H, ldh, cs, sn, g, h1, h2, scal + 2, j, scal);
+            givens_kernel<<<1, kMaxRestart, 0, s>>>(H, ldh, cs, sn, g, h1, h2, scal + 2, j, scal);
             scale_inv_kernel<<<gb, 256, 0, s>>>(n, w, scal + 1, w);
             ctx->launches += 2;
             SSD_TRY(launch_check(ctx, "arnoldi step"));
@@ -507,7 +508,7 @@ int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
     if (!(kr->tol > 0.0) || !isfinite(kr->tol)) return set_error(ctx, SSD_EINVAL, "tolerance must be positive");
     if (kr->maxit < 1) return set_error(ctx, SSD_EINVAL, "maxit must be >= 1");
     if (!kr->use_sa && (kr->restart < 1 || kr->restart > kMaxRestart))
-        return set_error(ctx, SSD_EINVAL, "restart must be in 1..256");
+        return set_error(ctx, SSD_EINVAL, "restart must be in 1..512");
     if (kr->prec != SSD_FP64 && kr->prec != SSD_FP32C) return set_error(ctx, SSD_EINVAL, "unknown precision");
     return SSD_OK;
 }
