@@ -13,6 +13,7 @@ quadrature.py  quadrature points and weights (Section 5.4, eq. Quadrature).
 solvers.py     GMRES, successive approximations, Darcy and Stokes solves,
                the Dirichlet-Neumann iteration (Sections 3 and 6).
 analytic.py    Joseph-Tao porous-sphere solution, drag, spectrum (Sections 4, 7.3).
+field.py       off-surface Darcy pressure and Stokes velocity (eqs. Greens, Stokes).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests
 (closed forms, identities, printed table values); none is "parity unpinned"
