@@ -327,6 +327,28 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
                        double *u_S, double *f_S, double drag[3], int *outer_its,
                        int *inner_its, double *res_hist, ssd_stream stream);
 
+/* ------------------------------------------------------ off-surface fields
+ * Field values away from the surface from the boundary data of a D-N solve
+ * (FP64, bare kernels; accurate for field points a few grid spacings from
+ * the surface: the paper gives no near-surface correction).  Field points
+ * targets[3][nt] and outputs are device arrays; nt may be 0.
+ *
+ * Darcy pressure inside the body, Green's representation (eq. Greens) with
+ * dp/dn = -(mu/kappa) q (Darcy's law, the interface flux q = u . n):
+ *   p_D(y) = (mu/kappa) sum_j w_j q_j G(y, x_j) + sum_j w_j p_j dG/dn(x_j),
+ *   G = -1/(4 pi r), dG/dn = -(y - x) . n / (4 pi r^3);  out[nt].
+ * Stokes velocity outside, eq. Stokes with n_S = -n and 1/(8 pi mu):
+ *   u_S(y) = U_inf - 1/(8 pi mu) sum_j w_j S(y - x_j) f_j
+ *            + 6/(8 pi) sum_j w_j (u_j . yh)(yh . n_j) yh / r^5;  out[3][nt].
+ * q, p_D, f, u are the outputs of ssd_ddm_solve.  Asynchronous on `stream`.
+ */
+int ssd_darcy_pressure_field(ssd_ctx *ctx, const ssd_points *pts, double mu, double kappa,
+                             const double *q, const double *p_D, int64_t nt, const double *targets,
+                             double *out, ssd_stream stream);
+int ssd_stokes_velocity_field(ssd_ctx *ctx, const ssd_points *pts, double mu,
+                              const double uinf[3] /* host */, const double *f, const double *u,
+                              int64_t nt, const double *targets, double *out, ssd_stream stream);
+
 /* ---------------------------------------------------------------- adjoint
  * Derivatives of a scalar output of the Dirichlet-Neumann solve with respect
  * to the two physical parameters of Sections 2 and 7, log(kappa) and gamma,

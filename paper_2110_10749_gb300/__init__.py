@@ -38,6 +38,7 @@ EXPORTS = [
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
+    "ssd_darcy_pressure_field", "ssd_stokes_velocity_field",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 FUNC_DRAG, FUNC_FLUX = 0, 1
@@ -143,6 +144,8 @@ def lib():
                                       C.POINTER(d), P, P, P, P],
         "ssd_geometry_gradient": [P, C.POINTER(CPoints), i, d, d, d, P, P, P, P, P, P],
         "ssd_shape_contract": [P, i64, i, P, P, P, P, P, P, C.POINTER(d), P],
+        "ssd_darcy_pressure_field": [P, C.POINTER(CPoints), d, d, P, P, i64, P, P, P],
+        "ssd_stokes_velocity_field": [P, C.POINTER(CPoints), d, C.POINTER(d), P, P, i64, P, P, P],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
         "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
@@ -460,6 +463,27 @@ def ddm_gradient(ctx, pts, prm, functional=FUNC_DRAG, raise_on_notconv=True):
     if st != SSD_ENOTCONV or raise_on_notconv:
         ctx.check(st, "ssd_ddm_gradient")
     return val.value, np.array(g[:]), st
+
+
+def darcy_pressure_field(ctx, pts, mu, kappa, q, p, targets, out=None):
+    """Darcy pressure at field points inside the body (targets (3, nt) CUDA tensor)."""
+    torch = _torch()
+    nt = int(targets.shape[1])
+    out = out if out is not None else torch.empty((nt,), dtype=torch.float64, device=targets.device)
+    ctx.check(lib().ssd_darcy_pressure_field(ctx.h, C.byref(pts.c), float(mu), float(kappa), _ptr(q), _ptr(p), nt,
+                                             _ptr(targets), _ptr(out), _stream()), "ssd_darcy_pressure_field")
+    return out
+
+
+def stokes_velocity_field(ctx, pts, mu, uinf, f, u, targets, out=None):
+    """Stokes velocity at field points outside the body (targets (3, nt) CUDA tensor)."""
+    torch = _torch()
+    nt = int(targets.shape[1])
+    out = out if out is not None else torch.empty((3, nt), dtype=torch.float64, device=targets.device)
+    ui = (C.c_double * 3)(*uinf)
+    ctx.check(lib().ssd_stokes_velocity_field(ctx.h, C.byref(pts.c), float(mu), ui, _ptr(f), _ptr(u), nt,
+                                              _ptr(targets), _ptr(out), _stream()), "ssd_stokes_velocity_field")
+    return out
 
 
 def geometry_gradient(ctx, pts, op, delta, a, b, mu=1.0, alpha=1.0, out=None):

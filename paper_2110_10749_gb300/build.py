@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssd.so")
-SOURCES = ["ctx.cu", "pair.cu", "quad.cu", "solve.cu", "batch.cu", "geom.cu"]
+SOURCES = ["ctx.cu", "pair.cu", "quad.cu", "solve.cu", "batch.cu", "geom.cu", "field.cu"]
 HEADERS = ["internal.h", "series_coef.h", "erfcx_coef.h", os.path.join("..", "..", "include", "ssd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS_EXTRA = []
