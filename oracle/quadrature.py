@@ -339,3 +339,117 @@ def star_points(clm, h: float, angle_deg: float = 70.0, center=(0.0, 0.0, 0.0)):
         "meta": np.ascontiguousarray(np.concatenate(ms, axis=1)),
         "h": h,
     }
+
+
+# ---------------------------------------------------------------- molecule
+#
+# The 'four-atom molecule' of Section 5.4 (eq. Molecule): sum_k exp(-|x - x_k|^2 / r^2) = c,
+# written as phi(x) = c - sum_k exp(-|x - x_k|^2 / r^2) so that phi > 0 outside and the outward
+# normal is grad(phi)/|grad(phi)|, grad(phi) = sum_k exp(-|x - x_k|^2/r^2) 2 (x - x_k) / r^2.
+# Roots along the grid lines follow the same fixed sampling and bisection as the star surfaces,
+# on [lo_i, hi_i] = [min_k x_k,i - D, max_k x_k,i + D] with D = 1.0625 r sqrt(log(n_atoms / c))
+# (a point farther than r sqrt(log(n_atoms/c)) from every centre has phi > 0).
+
+MOLECULE_CENTERS = (
+    (math.sqrt(3.0) / 3.0, 0.0, -math.sqrt(6.0) / 12.0),
+    (-math.sqrt(3.0) / 6.0, 0.5, -math.sqrt(6.0) / 12.0),
+    (-math.sqrt(3.0) / 6.0, -0.5, -math.sqrt(6.0) / 12.0),
+    (0.0, 0.0, math.sqrt(6.0) / 4.0),
+)
+
+
+def molecule_phi(centers, r, c, X):
+    s = 0.0 * X[0]
+    for xk in centers:
+        d2 = ((X[0] - xk[0]) ** 2 + (X[1] - xk[1]) ** 2) + (X[2] - xk[2]) ** 2
+        s = s + np.exp(-d2 / (r * r))
+    return c - s
+
+
+def molecule_normal(centers, r, c, X):
+    g = [0.0 * X[0], 0.0 * X[0], 0.0 * X[0]]
+    for xk in centers:
+        d = [X[k] - xk[k] for k in range(3)]
+        e = np.exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (r * r))
+        for k in range(3):
+            g[k] = g[k] + e * (2.0 * d[k] / (r * r))
+    gn = np.sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2])
+    return np.stack([g[k] / gn for k in range(3)])
+
+
+def molecule_points(h: float, angle_deg: float = 70.0, centers=MOLECULE_CENTERS, r: float = 0.5, c: float = 0.6):
+    """Quadrature set (eq. Quadrature) of the molecule surface (eq. Molecule);
+    same output and order as star_points."""
+    centers = [tuple(float(v) for v in xk) for xk in centers]
+    h = float(h)
+    ct = cos_threshold(angle_deg)
+    D = 1.0625 * r * math.sqrt(math.log(len(centers) / c))
+    lo = [min(xk[k] for xk in centers) - D for k in range(3)]
+    hi = [max(xk[k] for xk in centers) + D for k in range(3)]
+    ds = 1.0 / 64.0
+    xs, ns, ws, ms = [], [], [], []
+    for i in range(3):
+        a_, b_ = OTHER[i]
+        nk = int(math.ceil((hi[i] - lo[i]) / ds))
+        dt = (hi[i] - lo[i]) / nk
+        ja = np.arange(math.floor(lo[a_] / h) - 1, math.ceil(hi[a_] / h) + 2)
+        jb = np.arange(math.floor(lo[b_] / h) - 1, math.ceil(hi[b_] / h) + 2)
+        JA, JB = np.meshgrid(ja, jb, indexing="ij")
+        JA, JB = JA.ravel(), JB.ravel()
+        xa = JA.astype(np.float64) * h
+        xb = JB.astype(np.float64) * h
+        near = np.zeros(xa.size, dtype=bool)
+        for xk in centers:
+            near |= (xa - xk[a_]) ** 2 + (xb - xk[b_]) ** 2 < D * D
+        JA, JB, xa, xb = JA[near], JB[near], xa[near], xb[near]
+        T = lo[i] + np.arange(nk + 1, dtype=np.float64) * dt
+        L = xa.size
+
+        def phi_at(t, rows):
+            X = [None, None, None]
+            X[i] = t
+            X[a_] = xa[rows]
+            X[b_] = xb[rows]
+            return molecule_phi(centers, r, c, X)
+        Fv = phi_at(np.tile(T, L), np.repeat(np.arange(L), nk + 1)).reshape(L, nk + 1)
+        pos = Fv > 0.0
+        line, kk = np.nonzero(pos[:, :-1] != pos[:, 1:])
+        lo_t, hi_t = T[kk].copy(), T[kk + 1].copy()
+        flo, fhi = Fv[line, kk].copy(), Fv[line, kk + 1].copy()
+        slo = flo > 0.0
+        active = np.ones(lo_t.size, dtype=bool)
+        for _ in range(200):
+            mid = 0.5 * (lo_t + hi_t)
+            active &= ~((mid == lo_t) | (mid == hi_t))
+            idx = np.nonzero(active)[0]
+            if idx.size == 0:
+                break
+            fm = phi_at(mid[idx], line[idx])
+            same = (fm > 0.0) == slo[idx]
+            lo_t[idx[same]] = mid[idx[same]]
+            flo[idx[same]] = fm[same]
+            hi_t[idx[~same]] = mid[idx[~same]]
+            fhi[idx[~same]] = fm[~same]
+        t = np.where(np.abs(flo) <= np.abs(fhi), lo_t, hi_t)
+        first = np.r_[True, line[1:] != line[:-1]]
+        start = np.maximum.accumulate(np.where(first, np.arange(line.size), 0))
+        ordinal = np.arange(line.size) - start
+        P = np.empty((3, t.size))
+        P[i], P[a_], P[b_] = t, xa[line], xb[line]
+        nrm = molecule_normal(centers, r, c, P) if t.size else np.zeros((3, 0))
+        keep = np.abs(nrm[i]) >= ct
+        P, nrm = P[:, keep], nrm[:, keep]
+        psi = pou(nrm, angle_deg)[i]
+        w = psi * (h * h) / np.abs(nrm[i])
+        meta = np.stack([np.full(P.shape[1], i), JA[line][keep], JB[line][keep], ordinal[keep]]).astype(np.int32)
+        xs.append(P)
+        ns.append(nrm)
+        ws.append(w)
+        ms.append(meta)
+    return {
+        "xyz": np.ascontiguousarray(np.concatenate(xs, axis=1)),
+        "nrm": np.ascontiguousarray(np.concatenate(ns, axis=1)),
+        "w": np.ascontiguousarray(np.concatenate(ws)),
+        "meta": np.ascontiguousarray(np.concatenate(ms, axis=1)),
+        "h": h,
+    }
