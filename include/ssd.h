@@ -100,7 +100,12 @@ int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out /* host */);
  * sum_k c_k Y_k(xi).  The sum of |c_lm| sqrt((2l+1)/(4 pi)) must be < 1.
  * The paper's own examples are the sphere and the ellipsoid; star surfaces
  * are smooth test shapes of the same construction. */
-enum ssd_surface_kind { SSD_SPHERE = 0, SSD_ELLIPSOID = 1, SSD_STAR = 2 };
+enum ssd_surface_kind { SSD_SPHERE = 0, SSD_ELLIPSOID = 1, SSD_STAR = 2, SSD_MOLECULE = 3 };
+/* SSD_MOLECULE is the four-atom molecule of eq. Molecule, centres
+ * (sqrt3/3, 0, -sqrt6/12), (-sqrt3/6, +-1/2, -sqrt6/12), (0, 0, sqrt6/4) shifted by
+ * center, sum_k exp(-|x - x_k|^2/r^2) = c with r = abc[0], c = abc[1] (0 selects the
+ * paper's r = 0.5, c = 0.6).  Its roots follow the star surfaces' sampling and
+ * bisection on [min_k x_k,i - D, max_k x_k,i + D], D = 1.0625 r sqrt(log(4/c)). */
 typedef struct {
     int kind;
     double center[3];

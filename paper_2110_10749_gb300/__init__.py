@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libssd.so")
 
 SSD_OK, SSD_EINVAL, SSD_ENOMEM, SSD_ECUDA, SSD_ENOTCONV, SSD_ENUMERIC = range(6)
 FP64, FP32C = 0, 1
-SPHERE, ELLIPSOID, STAR = 0, 1, 2
+SPHERE, ELLIPSOID, STAR, MOLECULE = 0, 1, 2, 3
 TRACTION_BJS, TRACTION_JOSEPH_TAO = 0, 1
 K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_SLDL, K_LAPLACE_DL_T, K_STOKES_DL_T = range(8)
 
@@ -289,6 +289,11 @@ def quadrature_points(ctx, kind, abc=(1.0,), h=1 / 8, angle_deg=70.0, center=(0.
                                       _ptr(xyz), _ptr(nrm), _ptr(w), C.c_void_p(meta.data_ptr()), _stream()),
               "ssd_quadrature_points")
     return {"xyz": xyz, "nrm": nrm, "w": w, "meta": meta}
+
+
+def molecule_points(ctx, h, r=0.5, c=0.6, angle_deg=70.0, center=(0.0, 0.0, 0.0)):
+    """Quadrature points of the four-atom molecule (eq. Molecule)."""
+    return quadrature_points(ctx, MOLECULE, (r, c), h, angle_deg, center)
 
 
 def quadrature_jacobian(ctx, clm, h, n, angle_deg=70.0, center=(0.0, 0.0, 0.0)):

@@ -1,5 +1,6 @@
-// Quadrature points of Section 5.4 (eq. Quadrature) on spheres, ellipsoids
-// and star-shaped surfaces r(xi) = 1 + sum_{l<=4} c_lm Y_lm(xi).
+// Quadrature points of Section 5.4 (eq. Quadrature) on spheres, ellipsoids,
+// the four-atom molecule (eq. Molecule) and star-shaped surfaces
+// r(xi) = 1 + sum_{l<=4} c_lm Y_lm(xi).
 //
 // One thread per grid line.  A first pass counts the kept intersections per
 // line, an exclusive scan turns counts into output offsets, and a second pass
@@ -31,6 +32,10 @@ struct QuadGeo {
     double rb;            // bound of r: 1 + sum |c_k| B_l
     double tlo[3], dt[3]; // sample grid along the lines of each axis
     int nk;               // sample intervals per line
+    // molecule (eq. Molecule): atom centres, Gaussian width r, level c, reach D
+    double mol[4][3];
+    double mr, mc, mD;
+    int nka[3];           // sample intervals per line of each axis
     int *overflow;        // set when a line has more than kMaxRoots crossings
 };
 
@@ -278,9 +283,89 @@ __device__ int eval_line_star(const QuadGeo &g, int ax, int64_t ja, int64_t jb, 
     return kept;
 }
 
+// ----------------------------------------------------------------- molecule
+// phi = c - sum_k exp(-|x - x_k|^2 / r^2) (phi > 0 outside), grad phi =
+// sum_k exp(-|x - x_k|^2 / r^2) 2 (x - x_k) / r^2; the same sampling and
+// bisection as the star surfaces.
+__device__ double mol_phi(const QuadGeo &g, const double X[3]) {
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        const double d0 = X[0] - g.mol[k][0], d1 = X[1] - g.mol[k][1], d2 = X[2] - g.mol[k][2];
+        const double r2 = (d0 * d0 + d1 * d1) + d2 * d2;
+        s = s + exp(-r2 / (g.mr * g.mr));
+    }
+    return g.mc - s;
+}
+
+__device__ void mol_normal(const QuadGeo &g, const double X[3], double nv[3]) {
+    double G[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 4; ++k) {
+        const double d[3] = {X[0] - g.mol[k][0], X[1] - g.mol[k][1], X[2] - g.mol[k][2]};
+        const double e = exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (g.mr * g.mr));
+        for (int q = 0; q < 3; ++q) G[q] = G[q] + e * (2.0 * d[q] / (g.mr * g.mr));
+    }
+    const double gn = sqrt((G[0] * G[0] + G[1] * G[1]) + G[2] * G[2]);
+    for (int q = 0; q < 3; ++q) nv[q] = G[q] / gn;
+}
+
+__device__ int eval_line_molecule(const QuadGeo &g, int ax, int64_t ja, int64_t jb, double P[kMaxRoots][3],
+                                  double N[kMaxRoots][3], int br[kMaxRoots]) {
+    const int a = ax == 0 ? 1 : 0;
+    const int b = ax == 2 ? 1 : 2;
+    const double xa = (double)ja * g.h;
+    const double xb = (double)jb * g.h;
+    bool near = false;
+    for (int k = 0; k < 4; ++k) {
+        const double da = xa - g.mol[k][a], db = xb - g.mol[k][b];
+        near |= da * da + db * db < g.mD * g.mD;
+    }
+    if (!near) return 0;
+    double X[3];
+    X[a] = xa;
+    X[b] = xb;
+    X[ax] = g.tlo[ax];
+    double fprev = mol_phi(g, X);
+    double tprev = g.tlo[ax];
+    int kept = 0, ordinal = 0;
+    for (int k = 1; k <= g.nka[ax]; ++k) {
+        const double t = g.tlo[ax] + (double)k * g.dt[ax];
+        X[ax] = t;
+        const double f = mol_phi(g, X);
+        if ((fprev > 0.0) != (f > 0.0)) {
+            double lo = tprev, hi = t, flo = fprev, fhi = f;
+            const bool slo = flo > 0.0;
+            for (int it = 0; it < 200; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (mid == lo || mid == hi) break;
+                X[ax] = mid;
+                const double fm = mol_phi(g, X);
+                if ((fm > 0.0) == slo) { lo = mid; flo = fm; }
+                else { hi = mid; fhi = fm; }
+            }
+            X[ax] = fabs(flo) <= fabs(fhi) ? lo : hi;
+            double nv[3];
+            mol_normal(g, X, nv);
+            if (fabs(nv[ax]) >= g.ct) {
+                if (kept == kMaxRoots) {
+                    atomicExch(g.overflow, 1);
+                } else {
+                    for (int q = 0; q < 3; ++q) { P[kept][q] = X[q]; N[kept][q] = nv[q]; }
+                    br[kept] = ordinal;
+                    ++kept;
+                }
+            }
+            ++ordinal;
+        }
+        fprev = f;
+        tprev = t;
+    }
+    return kept;
+}
+
 __device__ __forceinline__ int eval_any(const QuadGeo &g, int ax, int64_t ja, int64_t jb, double P[kMaxRoots][3],
                                         double N[kMaxRoots][3], int br[kMaxRoots]) {
     if (g.kind == SSD_STAR) return eval_line_star(g, ax, ja, jb, P, N, br);
+    if (g.kind == SSD_MOLECULE) return eval_line_molecule(g, ax, ja, jb, P, N, br);
     return eval_line(g, ax, ja, jb, P, N, br);
 }
 
@@ -470,10 +555,39 @@ int quad_geometry(ssd_ctx *ctx, const ssd_surface *surf, double h, double angle_
         for (int k = 0; k < 3; ++k) g.A[k] = rb;
         const double ds = 1.0 / 64.0;
         g.nk = (int)ceil(2.125 * rb / ds);
+    } else if (surf->kind == SSD_MOLECULE) {
+        // the four-atom molecule of Section 5.4 about surf->center
+        const double r = surf->abc[0] > 0.0 ? surf->abc[0] : 0.5;
+        const double c = surf->abc[1] > 0.0 ? surf->abc[1] : 0.6;
+        if (!isfinite(r) || !isfinite(c) || !(c < 4.0))
+            return set_error(ctx, SSD_EINVAL, "molecule width r must be positive and level c in (0, 4)");
+        const double s3 = sqrt(3.0), s6 = sqrt(6.0);
+        const double cen[4][3] = {{s3 / 3.0, 0.0, -s6 / 12.0}, {-s3 / 6.0, 0.5, -s6 / 12.0},
+                                  {-s3 / 6.0, -0.5, -s6 / 12.0}, {0.0, 0.0, s6 / 4.0}};
+        g.mr = r;
+        g.mc = c;
+        g.mD = 1.0625 * r * sqrt(log(4.0 / c));
+        const double ds = 1.0 / 64.0;
+        for (int k = 0; k < 3; ++k) {
+            double lo = 1e300, hi = -1e300;
+            for (int a = 0; a < 4; ++a) {
+                g.mol[a][k] = cen[a][k] + surf->center[k];
+                lo = fmin(lo, g.mol[a][k]);
+                hi = fmax(hi, g.mol[a][k]);
+            }
+            lo = lo - g.mD;
+            hi = hi + g.mD;
+            g.nka[k] = (int)ceil((hi - lo) / ds);
+            g.tlo[k] = lo;
+            g.dt[k] = (hi - lo) / g.nka[k];
+            g.c[k] = 0.5 * (lo + hi);      // line ranges only
+            g.A[k] = 0.5 * (hi - lo) + 1e-9;   // covers [lo, hi] despite rounding
+        }
     } else {
         return set_error(ctx, SSD_EINVAL, "unknown surface kind");
     }
     for (int k = 0; k < 3; ++k) {
+        if (g.kind == SSD_MOLECULE) continue;
         g.c[k] = surf->center[k];
         if (!(g.A[k] > 0.0) || !isfinite(g.A[k]) || !isfinite(g.c[k]))
             return set_error(ctx, SSD_EINVAL, "semi-axes must be positive and finite");
