@@ -111,10 +111,11 @@ def weighted_mean(pts, v):
     return float(pts["w"] @ v) / float(pts["w"].sum())
 
 
-def darcy_solve(pts, delta, mu, kappa, q, tol=1e-9, restart=50, maxit=1000, use_sa=False):
+def darcy_solve(pts, delta, mu, kappa, q, tol=1e-9, restart=50, maxit=1000, use_sa=False, x0=None):
     """Solve -D^L p = (mu/kappa) L q for the Darcy pressure on the interface.
 
     Returns (p, iterations, relres).  p has zero quadrature-weighted mean.
+    x0: initial iterate (zero when None).
     """
     b = (mu / kappa) * oracle.laplace_sl(pts, delta, q)
     if use_sa:
@@ -123,7 +124,7 @@ def darcy_solve(pts, delta, mu, kappa, q, tol=1e-9, restart=50, maxit=1000, use_
         def step(p):
             pn = p + oracle.laplace_dl(pts, delta, p) + b
             return pn - weighted_mean(pts, pn)
-        p, its, rel = successive_approx(step, np.zeros_like(b), tol, maxit)
+        p, its, rel = successive_approx(step, np.zeros_like(b) if x0 is None else x0, tol, maxit)
     else:
         # -D^L annihilates constants.  The rank-one term 1 (w . p) / sum(w)
         # makes the operator nonsingular; for a right-hand side in the range
@@ -131,7 +132,7 @@ def darcy_solve(pts, delta, mu, kappa, q, tol=1e-9, restart=50, maxit=1000, use_
         W = float(pts["w"].sum())
         wv = pts["w"]
         p, its, rel = gmres(lambda p: -oracle.laplace_dl(pts, delta, p) + float(wv @ p) / W,
-                            b, tol, restart, maxit)
+                            b, tol, restart, maxit, x0=x0)
     return p - weighted_mean(pts, p), its, rel
 
 
@@ -141,7 +142,8 @@ def normal_flux_term(pts, u):
     return n * (float(pts["w"] @ (u * n).sum(0)) / float(pts["w"].sum()))
 
 
-def stokes_solve(pts, delta, mu, f, uinf, tol=1e-9, restart=50, maxit=1000, use_sa=False, deflate=False):
+def stokes_solve(pts, delta, mu, f, uinf, tol=1e-9, restart=50, maxit=1000, use_sa=False, deflate=False,
+                 x0=None):
     """Solve (I - D^S) u = U_inf - M f for the interface velocity [3][N].
 
     deflate: the continuous I/2 - K has the normal field n in its null space,
@@ -154,15 +156,15 @@ def stokes_solve(pts, delta, mu, f, uinf, tol=1e-9, restart=50, maxit=1000, use_
     if use_sa:
         # eq. Stokes_BIEM_iter: u <- u/2 + K u + b = D^S u + b
         return successive_approx(lambda u: oracle.stokes_dl(pts, delta, u) + b,
-                                 np.zeros_like(b), tol, maxit)
+                                 np.zeros_like(b) if x0 is None else x0, tol, maxit)
     if deflate:
         return gmres(lambda u: u - oracle.stokes_dl(pts, delta, u) + normal_flux_term(pts, u), b, tol,
-                     restart, maxit)
-    return gmres(lambda u: u - oracle.stokes_dl(pts, delta, u), b, tol, restart, maxit)
+                     restart, maxit, x0=x0)
+    return gmres(lambda u: u - oracle.stokes_dl(pts, delta, u), b, tol, restart, maxit, x0=x0)
 
 
 def stokes_solve_bjs_implicit(pts, delta, mu, p, uinf, kappa, gamma, sign=1.0, tol=1e-9, restart=50,
-                              maxit=1000, deflate=False):
+                              maxit=1000, deflate=False, x0=None):
     """Stokes solve with the BJS slip term taken at the current velocity.
 
     With f = -p n + s c P u (c = gamma/sqrt(kappa), P u = u - (u.n) n),
@@ -177,7 +179,7 @@ def stokes_solve_bjs_implicit(pts, delta, mu, p, uinf, kappa, gamma, sign=1.0, t
         Pu = u - (u * n).sum(0) * n
         v = u - oracle.stokes_dl(pts, delta, u) + c * oracle.stokes_sl(pts, delta, mu, Pu)
         return v + normal_flux_term(pts, u) if deflate else v
-    return gmres(A, b, tol, restart, maxit)
+    return gmres(A, b, tol, restart, maxit, x0=x0)
 
 
 def traction_bjs(pts, p, u_prev, kappa, gamma, sign=1.0):
@@ -200,7 +202,7 @@ def traction_joseph_tao(pts, p, R, kappa, mu, uinf):
 def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
               outer="sa", traction="bjs", R=1.0, bjs_sign=1.0,
               inner_tol=None, restart=50, inner_maxit=1000, use_sa=False, bjs_implicit=False,
-              deflate=False):
+              deflate=False, warm_inner=False):
     """Dirichlet-Neumann iteration of Sections 3 and 6.
 
     One sweep G maps (q, u_prev) to (q_new, u): Darcy solve with Neumann data
@@ -216,6 +218,8 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
     (see stokes_solve_bjs_implicit) instead of the previous sweep's, so the
     interface state is q alone.
     deflate: Stokes solves remove the near-null normal mode (see stokes_solve).
+    warm_inner: with outer="sa", each local solve starts from the previous
+    sweep's solution (Darcy from p, Stokes from u) instead of zero.
     Returns a dict with q, p, u, f, drag, outer iteration count, inner counts
     and the residual history.
     """
@@ -227,11 +231,18 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
     stacked = (traction == "bjs" and gamma != 0.0 and not bjs_implicit)
     inner_its = []
 
+    warm = {"p": None}
+
     def sweep(q, u_prev):
-        p, itd, _ = darcy_solve(pts, delta, mu, kappa, q, inner_tol, restart, inner_maxit, use_sa)
+        wstart = warm_inner and outer == "sa"
+        p, itd, _ = darcy_solve(pts, delta, mu, kappa, q, inner_tol, restart, inner_maxit, use_sa,
+                                x0=warm["p"] if wstart else None)
+        if wstart:
+            warm["p"] = p
+        u0 = u_prev if wstart else None
         if traction == "bjs" and bjs_implicit:
             u, its, _ = stokes_solve_bjs_implicit(pts, delta, mu, p, uinf, kappa, gamma, bjs_sign,
-                                                  inner_tol, restart, inner_maxit, deflate)
+                                                  inner_tol, restart, inner_maxit, deflate, x0=u0)
             f = traction_bjs(pts, p, u, kappa, gamma, bjs_sign)
         else:
             if traction == "bjs":
@@ -239,7 +250,7 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
             else:
                 f = traction_joseph_tao(pts, p, R, kappa, mu, uinf)
             u, its, _ = stokes_solve(pts, delta, mu, f, uinf, inner_tol, restart, inner_maxit, use_sa,
-                                     deflate)
+                                     deflate, x0=u0)
         inner_its.append((itd, its))
         qn = (1.0 - theta) * q + theta * (u * n).sum(0)
         return qn, u, p, f
