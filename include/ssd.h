@@ -253,6 +253,11 @@ typedef struct {
                       rounding, most of all in FP32C; the rank-one term removes it and
                       selects the zero-net-flux solution (int u.n dS = 0, the Darcy
                       compatibility condition).  0 = the operator as printed. */
+    int warm;      /* 1: start from a previous solution instead of 0.  In relaxed D-N
+                      sweeps (outer_gmres = 0) each local solve starts from the previous
+                      sweep's solution; ssd_darcy_solve / ssd_stokes_solve start from
+                      the values already in their output array.  Ignored by the
+                      interface GMRES's sweeps. */
 } ssd_krylov;
 
 /*

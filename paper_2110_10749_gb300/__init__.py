@@ -70,7 +70,7 @@ class CSurface(C.Structure):
 
 class CKrylov(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("restart", C.c_int), ("use_sa", C.c_int),
-                ("prec", C.c_int), ("deflate", C.c_int)]
+                ("prec", C.c_int), ("deflate", C.c_int), ("warm", C.c_int)]
 
 
 class CDdmParams(C.Structure):
@@ -372,8 +372,9 @@ def laplace_SLDL(ctx, pts, delta, g, p, alpha=1.0, beta=1.0, prec=FP64, out=None
     return out
 
 
-def krylov(tol=1e-9, maxit=200, restart=50, use_sa=False, prec=FP64, deflate=False):
-    return CKrylov(float(tol), int(maxit), int(restart), 1 if use_sa else 0, int(prec), 1 if deflate else 0)
+def krylov(tol=1e-9, maxit=200, restart=50, use_sa=False, prec=FP64, deflate=False, warm=False):
+    return CKrylov(float(tol), int(maxit), int(restart), 1 if use_sa else 0, int(prec), 1 if deflate else 0,
+                   1 if warm else 0)
 
 
 def darcy_solve(ctx, pts, delta, mu, kappa, q, kr=None, out=None):

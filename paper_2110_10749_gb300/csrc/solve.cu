@@ -474,13 +474,13 @@ int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double
 
 // Successive approximations x <- step(x) until ||x_k - x_{k-1}|| <= tol ||x_k||.
 int successive(ssd_ctx *ctx, cudaStream_t s, int64_t n, const std::function<int(const double *, double *)> &step,
-               double *x, double tol, int maxit, GmresResult *res) {
+               double *x, double tol, int maxit, GmresResult *res, bool warm = false) {
     Buf xn, scal;
     SSD_TRY(xn.alloc(ctx, sizeof(double) * n));
     SSD_TRY(scal.alloc(ctx, sizeof(double) * 4));
     Dots dots;
     SSD_TRY(dots.init(ctx, s, 2));
-    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
+    if (!warm) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
     const unsigned gb = grid_for(n);
     for (int it = 1; it <= maxit; ++it) {
         SSD_TRY(step(x, xn.d()));
@@ -516,7 +516,7 @@ int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
 // ------------------------------------------------------------- local solves
 int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu, double kappa,
                      const double *q, double *p, const ssd_krylov &kr, GmresResult *res, cudaStream_t s,
-                     bool gauge = true) {
+                     bool gauge = true, bool warm = false) {
     const int64_t n = pts->n;
     Buf b, scal;
     SSD_TRY(b.alloc(ctx, sizeof(double) * n));
@@ -542,7 +542,7 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
             ctx->launches++;
             return launch_check(ctx, "darcy sa step");
         };
-        st = successive(ctx, s, n, step, p, kr.tol, kr.maxit, res);
+        st = successive(ctx, s, n, step, p, kr.tol, kr.maxit, res, warm);
     } else {
         // -D^L p + (w . p)/sum(w): nonsingular, same solution for consistent b
         auto A = [&](const double *x, double *y) -> int {
@@ -551,7 +551,7 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
             a.rank1_weight_mean = true; a.out = y;
             return pair_apply(ctx, L, a, s);
         };
-        st = gmres(ctx, s, n, A, b.d(), p, kr.tol, kr.restart, kr.maxit, false, res);
+        st = gmres(ctx, s, n, A, b.d(), p, kr.tol, kr.restart, kr.maxit, warm, res);
     }
     if (st != SSD_OK && st != SSD_ENOTCONV) return st;
     if (!gauge) return st;
@@ -567,7 +567,7 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
 
 int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
                       const double *f, const double uinf[3], double *u, const ssd_krylov &kr, GmresResult *res,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool warm = false) {
     const int64_t n = pts->n;
     Buf b;
     SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
@@ -586,7 +586,7 @@ int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doub
             ctx->launches++;
             return launch_check(ctx, "stokes sa step");
         };
-        return successive(ctx, s, 3 * n, step, u, kr.tol, kr.maxit, res);
+        return successive(ctx, s, 3 * n, step, u, kr.tol, kr.maxit, res, warm);
     }
     // (I - D^S) u  [+ n (w . (u.n))/sum(w) when deflating]
     auto A = [&](const double *x, double *y) -> int {
@@ -596,7 +596,7 @@ int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doub
         a.out = y;
         return pair_apply(ctx, L, a, s);
     };
-    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, false, res);
+    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
 }
 
 // Stokes step with the BJS slip at its own velocity: with f = -p n + c P u
@@ -605,7 +605,7 @@ int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doub
 // the matvec is one fused single+double layer pass.
 int stokes_solve_bjs_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
                           const double *p, const double uinf[3], double c, double *u, const ssd_krylov &kr,
-                          GmresResult *res, cudaStream_t s) {
+                          GmresResult *res, cudaStream_t s, bool warm = false) {
     const int64_t n = pts->n;
     Buf b, tmp;
     SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
@@ -625,7 +625,7 @@ int stokes_solve_bjs_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, 
         a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
         return pair_apply(ctx, L, a, s);
     };
-    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, false, res);
+    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
 }
 
 // ------------------------------------------------------------------ D-N solve
@@ -643,12 +643,18 @@ struct Ddm {
     // one sweep: (q, uprev) -> (qn, u); p and f are left in pbuf and f
     int sweep(const double *q, const double *uprev, double *qn, double *u, double *p) {
         GmresResult rd, rs;
-        int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s);
+        // relaxed sweeps may start each local solve from the previous sweep's
+        // solution (p keeps it; u starts from uprev)
+        const bool warm = P.inner.warm && !P.outer_gmres;
+        if (warm && u != uprev)
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u, uprev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s),
+                               "warm start copy"));
+        int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s, true, warm);
         if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
         SSD_TRY(st);
         if (P.traction_mode == SSD_TRACTION_BJS && P.bjs_implicit) {
             const double coef = P.bjs_sign * P.gamma / sqrt(P.kappa);
-            st = stokes_solve_bjs_impl(ctx, pts, *L, P.delta, P.mu, p, P.uinf, coef, u, P.inner, &rs, s);
+            st = stokes_solve_bjs_impl(ctx, pts, *L, P.delta, P.mu, p, P.uinf, coef, u, P.inner, &rs, s, warm);
             if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
             SSD_TRY(st);
             traction_bjs_kernel<<<grid_for(n), 256, 0, s>>>(n, p, u, pts->nrm, coef, f.d());
@@ -671,7 +677,7 @@ struct Ddm {
         }
         ctx->launches++;
         SSD_TRY(launch_check(ctx, "traction"));
-        st = stokes_solve_impl(ctx, pts, *L, P.delta, P.mu, f.d(), P.uinf, u, P.inner, &rs, s);
+        st = stokes_solve_impl(ctx, pts, *L, P.delta, P.mu, f.d(), P.uinf, u, P.inner, &rs, s, warm);
         if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
         SSD_TRY(st);
         q_update_kernel<<<grid_for(n), 256, 0, s>>>(n, P.theta, q, u, pts->nrm, qn);
@@ -719,6 +725,7 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     SSD_TRY(p.alloc(ctx, sizeof(double) * n));
     SSD_TRY(u.alloc(ctx, sizeof(double) * 3 * n));
     SSD_TRY(cuda_check(ctx, cudaMemsetAsync(z.d(), 0, sizeof(double) * 4 * n, s), "memset"));
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(p.d(), 0, sizeof(double) * n, s), "memset"));
     Dots dots;
     SSD_TRY(dots.init(ctx, s, 2));
     int its = 0;
@@ -1335,7 +1342,7 @@ int ssd_darcy_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu
     LayoutRef lref;
     SSD_TRY(get_layout(ctx, pts, &lref, s));
     GmresResult r;
-    const int st = darcy_solve_impl(ctx, pts, *lref.L, delta, mu, kappa, q, p_out, *kr, &r, s);
+    const int st = darcy_solve_impl(ctx, pts, *lref.L, delta, mu, kappa, q, p_out, *kr, &r, s, true, kr->warm != 0);
     if (iters) *iters = r.iters;
     if (relres) *relres = r.relres;
     if (st == SSD_OK || st == SSD_ENOTCONV) cudaStreamSynchronize(s);
@@ -1356,7 +1363,7 @@ int ssd_stokes_solve(ssd_ctx *ctx, const ssd_points *pts, double delta, double m
     LayoutRef lref;
     SSD_TRY(get_layout(ctx, pts, &lref, s));
     GmresResult r;
-    const int st = stokes_solve_impl(ctx, pts, *lref.L, delta, mu, f, uinf, u_out, *kr, &r, s);
+    const int st = stokes_solve_impl(ctx, pts, *lref.L, delta, mu, f, uinf, u_out, *kr, &r, s, kr->warm != 0);
     if (iters) *iters = r.iters;
     if (relres) *relres = r.relres;
     if (st == SSD_OK || st == SSD_ENOTCONV) cudaStreamSynchronize(s);
