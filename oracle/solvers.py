@@ -202,7 +202,7 @@ def traction_joseph_tao(pts, p, R, kappa, mu, uinf):
 def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
               outer="sa", traction="bjs", R=1.0, bjs_sign=1.0,
               inner_tol=None, restart=50, inner_maxit=1000, use_sa=False, bjs_implicit=False,
-              deflate=False, warm_inner=False):
+              deflate=False, warm_inner=False, arnoldi=0):
     """Dirichlet-Neumann iteration of Sections 3 and 6.
 
     One sweep G maps (q, u_prev) to (q_new, u): Darcy solve with Neumann data
@@ -220,6 +220,11 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
     deflate: Stokes solves remove the near-null normal mode (see stokes_solve).
     warm_inner: with outer="sa", each local solve starts from the previous
     sweep's solution (Darcy from p, Stokes from u) instead of zero.
+    arnoldi > 0: no solve; instead `arnoldi` Arnoldi steps (modified
+    Gram-Schmidt) on the discrete iteration matrix A~ v = F(v) - F(0)
+    (eq. A_mat, Section 6) from the start vector frac(i g) - 1/2 (normalised,
+    i the point index, g = 0.6180339887498949), with Gram-Schmidt twice;
+    returns {"H": Hessenberg [m+1][m], "ritz": eigenvalues of H[:m, :m]}.
     Returns a dict with q, p, u, f, drag, outer iteration count, inner counts
     and the residual history.
     """
@@ -280,6 +285,26 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
 
         z0 = np.zeros(4 * N if stacked else N)
         c = F(z0)
+        if arnoldi > 0:
+            assert not stacked, "the iteration matrix acts on q alone"
+            # start vector with every mode present: v_i = frac(i g) - 1/2, g the golden section
+            v = np.mod(np.arange(N, dtype=np.float64) * 0.6180339887498949, 1.0) - 0.5
+            V = [v / np.linalg.norm(v)]
+            H = np.zeros((arnoldi + 1, arnoldi))
+            m = arnoldi
+            for j in range(arnoldi):
+                w = F(V[j]) - c
+                for _ in range(2):           # Gram-Schmidt twice (orthogonality to working precision)
+                    for i in range(j + 1):
+                        hij = float(V[i] @ w)
+                        H[i, j] += hij
+                        w = w - hij * V[i]
+                H[j + 1, j] = float(np.linalg.norm(w))
+                if H[j + 1, j] <= 1e-12 * float(np.abs(H[:j + 1, j]).max()):
+                    m = j + 1          # an invariant subspace: its Ritz values are eigenvalues
+                    break
+                V.append(w / H[j + 1, j])
+            return {"H": H[:m + 1, :m], "ritz": np.linalg.eigvals(H[:m, :m])}
         z, its, rel = gmres(lambda v: v - (F(v) - c), c, tol, restart=max(restart, maxit), maxit=maxit)
         hist.append(rel)
         if stacked:
