@@ -337,6 +337,22 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
                        double *u_S, double *f_S, double drag[3], int *outer_its,
                        int *inner_its, double *res_hist, ssd_stream stream);
 
+/*
+ * Spectrum of the discrete iteration matrix of the D-N sweeps (eq. A_mat,
+ * Section 6; Fig. 5): m Arnoldi steps (Gram-Schmidt twice) on
+ * A~ v = F(v) - F(0), F one relaxed sweep with prm's theta, from the start
+ * vector v_i = frac(0.6180339887498949 i) - 1/2 (all modes present), then the
+ * eigenvalues of the m x m Hessenberg block by the double-shifted QR
+ * iteration on the host.  Stops early (invariant subspace) when a new
+ * vector's norm falls below 1e-12 of its column.  Outputs (host):
+ * *m_out steps taken, ritz_re/ritz_im[m] (first *m_out valid), H[(m+1) * m]
+ * column-major (may be NULL).  m in 1..512; the lagged BJS slip with
+ * gamma != 0 is not supported (its iteration acts on (q, u)).  Synchronises
+ * `stream`.
+ */
+int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m,
+                     int *m_out, double *ritz_re, double *ritz_im, double *H, ssd_stream stream);
+
 /* ------------------------------------------------------ off-surface fields
  * Field values away from the surface from the boundary data of a D-N solve
  * (FP64, bare kernels; accurate for field points a few grid spacings from

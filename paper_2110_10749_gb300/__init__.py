@@ -38,7 +38,7 @@ EXPORTS = [
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
-    "ssd_darcy_pressure_field", "ssd_stokes_velocity_field",
+    "ssd_darcy_pressure_field", "ssd_stokes_velocity_field", "ssd_ddm_spectrum",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 FUNC_DRAG, FUNC_FLUX = 0, 1
@@ -145,6 +145,8 @@ def lib():
         "ssd_geometry_gradient": [P, C.POINTER(CPoints), i, d, d, d, P, P, P, P, P, P],
         "ssd_shape_contract": [P, i64, i, P, P, P, P, P, P, C.POINTER(d), P],
         "ssd_darcy_pressure_field": [P, C.POINTER(CPoints), d, d, P, P, i64, P, P, P],
+        "ssd_ddm_spectrum": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(i), C.POINTER(d),
+                             C.POINTER(d), C.POINTER(d), P],
         "ssd_stokes_velocity_field": [P, C.POINTER(CPoints), d, C.POINTER(d), P, P, i64, P, P, P],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
@@ -469,6 +471,21 @@ def ddm_gradient(ctx, pts, prm, functional=FUNC_DRAG, raise_on_notconv=True):
     if st != SSD_ENOTCONV or raise_on_notconv:
         ctx.check(st, "ssd_ddm_gradient")
     return val.value, np.array(g[:]), st
+
+
+def ddm_spectrum(ctx, pts, prm, m=50):
+    """Ritz values of the discrete D-N iteration matrix (eq. A_mat) from m
+    Arnoldi steps: (complex numpy array, Hessenberg (m+1, m) numpy array)."""
+    mo = C.c_int()
+    re = (C.c_double * m)()
+    im = (C.c_double * m)()
+    H = (C.c_double * ((m + 1) * m))()
+    ctx.check(lib().ssd_ddm_spectrum(ctx.h, C.byref(pts.c), C.byref(prm), int(m), C.byref(mo), re, im, H,
+                                     _stream()), "ssd_ddm_spectrum")
+    k = mo.value
+    ritz = np.array(re[:k]) + 1j * np.array(im[:k])
+    Hm = np.array(H[:]).reshape(m, m + 1).T[:k + 1, :k]
+    return ritz, Hm
 
 
 def darcy_pressure_field(ctx, pts, mu, kappa, q, p, targets, out=None):

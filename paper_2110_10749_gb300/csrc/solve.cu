@@ -804,6 +804,217 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     return status;
 }
 
+// ------------------------------------------------- discrete iteration matrix
+// Eigenvalues of a real upper Hessenberg matrix a (n x n, column-major,
+// overwritten) by the implicitly double-shifted QR iteration: deflate at
+// negligible subdiagonal entries (absolute, neighbour-gap and, for windows
+// stuck on clustered eigenvalues, 1e-11 relative tests), read off 1x1 and
+// 2x2 blocks, otherwise
+// chase a bulge started from the first column of (H - s1)(H - s2), s1, s2 the
+// eigenvalues of the trailing 2x2 block (ad hoc shifts every tenth step).
+// Only the active window is transformed (enough for eigenvalues).
+static int hessenberg_eigenvalues(int n, double *a, double *wr, double *wi) {
+    auto A = [&](int i, int j) -> double & { return a[i + (size_t)j * n]; };
+    double anorm = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i <= (j + 1 < n ? j + 1 : n - 1); ++i) anorm += fabs(A(i, j));
+    if (anorm == 0.0) anorm = 1.0;
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, iter = 0, total = 0;
+    while (hi >= 0) {
+        int l = hi;
+        for (; l > 0; --l) {
+            double sc = fabs(A(l - 1, l - 1)) + fabs(A(l, l));
+            if (sc == 0.0) sc = anorm;
+            const double h = fabs(A(l, l - 1));
+            if (h <= eps * sc) { A(l, l - 1) = 0.0; break; }
+            // the coupling is also negligible when the off-diagonal pair's
+            // product is small against the gap of the neighbouring diagonal
+            // entries (the test of Ahues and Tisseur)
+            const double ab = fmax(h, fabs(A(l - 1, l))), ba = fmin(h, fabs(A(l - 1, l)));
+            const double gap = fabs(A(l - 1, l - 1) - A(l, l));
+            const double aa = fmax(fabs(A(l, l)), gap), bb = fmin(fabs(A(l, l)), gap);
+            const double s2 = aa + ab;
+            if (ba * (ab / s2) <= fmax(1e-300, eps * (bb * (aa / s2)))) { A(l, l - 1) = 0.0; break; }
+            // clustered eigenvalues can leave a window stuck at rounding level
+            if (iter >= 30 && h <= 1e-11 * sc) { A(l, l - 1) = 0.0; break; }
+        }
+        if (l == hi) {
+            wr[hi] = A(hi, hi);
+            wi[hi] = 0.0;
+            --hi;
+            iter = 0;
+            continue;
+        }
+        if (l == hi - 1) {
+            const double p = A(hi - 1, hi - 1), q = A(hi - 1, hi), r = A(hi, hi - 1), t = A(hi, hi);
+            const double m = 0.5 * (p + t), d = 0.5 * (p - t);
+            const double disc = d * d + q * r;
+            if (disc >= 0.0) {
+                const double sq = sqrt(disc);
+                const double e1 = m + (m >= 0.0 ? sq : -sq);
+                const double det = p * t - q * r;
+                const double e2 = e1 != 0.0 ? det / e1 : m - sq;
+                wr[hi - 1] = e1; wr[hi] = e2;
+                wi[hi - 1] = wi[hi] = 0.0;
+            } else {
+                const double sq = sqrt(-disc);
+                wr[hi - 1] = wr[hi] = m;
+                wi[hi - 1] = sq;
+                wi[hi] = -sq;
+            }
+            hi -= 2;
+            iter = 0;
+            continue;
+        }
+        if (++total > 100 * n) return -1;
+        ++iter;
+        double sh, tt;
+        if (iter % 10 == 0) {
+            const double w = fabs(A(hi, hi - 1)) + fabs(A(hi - 1, hi - 2));
+            const double m1 = A(hi, hi) + 0.75 * w, m2 = A(hi, hi) - 0.4375 * w;
+            sh = m1 + m2;
+            tt = m1 * m2;
+        } else {
+            sh = A(hi - 1, hi - 1) + A(hi, hi);
+            tt = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);
+        }
+        double x = A(l, l) * A(l, l) + A(l, l + 1) * A(l + 1, l) - sh * A(l, l) + tt;
+        double y = A(l + 1, l) * (A(l, l) + A(l + 1, l + 1) - sh);
+        double z = A(l + 1, l) * A(l + 2, l + 1);
+        for (int k = l; k <= hi - 2; ++k) {
+            // reflector I - 2 v v^T / (v^T v) taking (x, y, z) to (alpha, 0, 0)
+            const double nv = sqrt(x * x + y * y + z * z);
+            if (nv != 0.0) {
+                const double alpha = x >= 0.0 ? -nv : nv;
+                const double v0 = x - alpha, v1 = y, v2 = z;
+                const double beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+                const int c0 = k > l ? k - 1 : l;
+                for (int j = c0; j <= hi; ++j) {
+                    const double f = beta * (v0 * A(k, j) + v1 * A(k + 1, j) + v2 * A(k + 2, j));
+                    A(k, j) -= f * v0;
+                    A(k + 1, j) -= f * v1;
+                    A(k + 2, j) -= f * v2;
+                }
+                const int r1 = k + 3 < hi ? k + 3 : hi;
+                for (int i = l; i <= r1; ++i) {
+                    const double f = beta * (v0 * A(i, k) + v1 * A(i, k + 1) + v2 * A(i, k + 2));
+                    A(i, k) -= f * v0;
+                    A(i, k + 1) -= f * v1;
+                    A(i, k + 2) -= f * v2;
+                }
+            }
+            x = A(k + 1, k);
+            y = A(k + 2, k);
+            if (k < hi - 2) z = A(k + 3, k);
+        }
+        // last rotation on rows/columns hi-1, hi
+        const double nr = hypot(x, y);
+        if (nr != 0.0) {
+            const double c = x / nr, sn = y / nr;
+            for (int j = hi - 2; j <= hi; ++j) {
+                const double u = A(hi - 1, j), v = A(hi, j);
+                A(hi - 1, j) = c * u + sn * v;
+                A(hi, j) = -sn * u + c * v;
+            }
+            for (int i = l; i <= hi; ++i) {
+                const double u = A(i, hi - 1), v = A(i, hi);
+                A(i, hi - 1) = c * u + sn * v;
+                A(i, hi) = -sn * u + c * v;
+            }
+        }
+    }
+    return 0;
+}
+
+// v_i = frac(i g) - 1/2 (g = 0.6180339887498949): a start vector with every mode present
+__global__ void golden_fill_kernel(int64_t n, double *v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double t = (double)i * 0.6180339887498949;
+        v[i] = (t - floor(t)) - 0.5;
+    }
+}
+
+// Ritz values of the discrete iteration matrix A~ v = F(v) - F(0), F one D-N
+// sweep (eq. A_mat), from m Arnoldi steps (Gram-Schmidt twice).
+int ddm_spectrum_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m, int *m_out,
+                      double *re, double *im, double *Hout, cudaStream_t s) {
+    SSD_TRY(check_ddm(ctx, prm));
+    if (m < 1 || m > kMaxRestart) return set_error(ctx, SSD_EINVAL, "m must be in 1..512");
+    if (!m_out || !re || !im) return set_error(ctx, SSD_EINVAL, "NULL output");
+    if (prm->traction_mode == SSD_TRACTION_BJS && prm->gamma != 0.0 && !prm->bjs_implicit)
+        return set_error(ctx, SSD_EINVAL, "the iteration matrix acts on q alone: lagged slip with gamma != 0 "
+                                          "is not supported");
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    Ddm D;
+    D.ctx = ctx; D.pts = pts; D.L = lref.L; D.P = *prm; D.P.outer_gmres = 1; D.s = s; D.n = pts->n;
+    const int64_t n = pts->n;
+    SSD_TRY(D.f.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(D.scal.alloc(ctx, sizeof(double) * 8));
+    Buf V, c, zero, u, p, small;
+    SSD_TRY(V.alloc(ctx, sizeof(double) * (size_t)(m + 1) * n));
+    SSD_TRY(c.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(zero.alloc(ctx, sizeof(double) * 4 * n));
+    SSD_TRY(u.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(p.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(small.alloc(ctx, sizeof(double) * (2 * (m + 3) + 8)));
+    double *h1 = small.d(), *h2 = h1 + m + 3, *scal = h2 + m + 3;
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(zero.d(), 0, sizeof(double) * 4 * n, s), "memset"));
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(p.d(), 0, sizeof(double) * n, s), "memset"));
+    SSD_TRY(D.sweep(zero.d(), zero.d() + n, c.d(), u.d(), p.d()));      // c = F(0)
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, m + 2));
+    const unsigned gb = grid_for(n);
+    golden_fill_kernel<<<gb, 256, 0, s>>>(n, V.d());
+    ctx->launches++;
+    SSD_TRY(dots.multi(V.d(), 0, 1, V.d(), n, scal));
+    sqrt_kernel<<<1, 32, 0, s>>>(scal);
+    scale_inv_kernel<<<gb, 256, 0, s>>>(n, V.d(), scal, V.d());
+    ctx->launches += 2;
+    std::vector<double> hh((size_t)(m + 1) * m, 0.0), c1(m + 2), c2(m + 2);
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+        double *vj = V.d() + (size_t)j * n, *w = V.d() + (size_t)(j + 1) * n;
+        SSD_TRY(D.sweep(vj, zero.d() + n, w, u.d(), p.d()));
+        axpby_kernel<<<gb, 256, 0, s>>>(n, -1.0, c.d(), 1.0, w);       // w = F(v_j) - F(0)
+        ctx->launches++;
+        SSD_TRY(dots.multi(V.d(), n, j + 1, w, n, h1));
+        vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h1, -1.0, w, n);
+        ctx->launches++;
+        SSD_TRY(dots.multi(V.d(), n, j + 1, w, n, h2));
+        vupdate_kernel<<<gb, 256, 0, s>>>(V.d(), n, j + 1, h2, -1.0, w, n);
+        ctx->launches++;
+        SSD_TRY(dots.multi(w, 0, 1, w, n, scal));
+        SSD_TRY(read_scalars(ctx, h1, j + 1, c1.data(), s));
+        SSD_TRY(read_scalars(ctx, h2, j + 1, c2.data(), s));
+        double nrm2;
+        SSD_TRY(read_scalars(ctx, scal, 1, &nrm2, s));
+        double cmax = 0.0;
+        for (int i = 0; i <= j; ++i) {
+            hh[i + (size_t)j * (m + 1)] = c1[i] + c2[i];
+            cmax = fmax(cmax, fabs(c1[i] + c2[i]));
+        }
+        const double hn = sqrt(fmax(nrm2, 0.0));
+        hh[(j + 1) + (size_t)j * (m + 1)] = hn;
+        if (!isfinite(hn)) return set_error(ctx, SSD_ENUMERIC, "non-finite Arnoldi vector");
+        if (hn <= 1e-12 * cmax) { mm = j + 1; break; }      // invariant subspace
+        axpby_kernel<<<gb, 256, 0, s>>>(n, 1.0 / hn, w, 0.0, w);
+        ctx->launches++;
+        SSD_TRY(launch_check(ctx, "arnoldi step"));
+    }
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "arnoldi sync"));
+    if (Hout)
+        for (size_t k = 0; k < hh.size(); ++k) Hout[k] = hh[k];
+    std::vector<double> sq((size_t)mm * mm);
+    for (int j = 0; j < mm; ++j)
+        for (int i = 0; i < mm; ++i) sq[i + (size_t)j * mm] = hh[i + (size_t)j * (m + 1)];
+    if (hessenberg_eigenvalues(mm, sq.data(), re, im) != 0)
+        return set_error(ctx, SSD_ENUMERIC, "Hessenberg QR iteration did not converge");
+    *m_out = mm;
+    return D.nonconv ? set_error(ctx, SSD_ENOTCONV, "a local solve reached its iteration limit") : SSD_OK;
+}
+
 // ------------------------------------------------------------------- adjoint
 // Discrete adjoint of the interface solve.  With the sweep written as
 //   p = P_g A_D^{-1} (mu/kappa) L q            (Darcy, gauge projection P_g)
@@ -1376,6 +1587,13 @@ int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     return ddm_impl(ctx, pts, prm, q, p_D, u_S, f_S, drag, outer_its, inner_its, res_hist, (cudaStream_t)stream);
+}
+
+int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m, int *m_out,
+                     double *ritz_re, double *ritz_im, double *H, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    return ddm_spectrum_impl(ctx, pts, prm, m, m_out, ritz_re, ritz_im, H, (cudaStream_t)stream);
 }
 
 int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional, double *value,

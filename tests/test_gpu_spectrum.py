@@ -1,0 +1,37 @@
+"""Spectrum of the discrete D-N iteration matrix (eq. A_mat, Fig. 5) on the
+device: Ritz values against the oracle's Arnoldi on the same map, against
+the eigenvalues of the returned Hessenberg matrix, and the n = 1 mode of the
+porous sphere against its closed form."""
+import numpy as np
+import pytest
+
+from oracle import quadrature as Q
+from oracle import solvers as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kappa,theta", [(1.0, 0.5), (1e-2, 0.005)])
+def test_spectrum_matches_oracle(gpu_ctx, kappa, theta):
+    import paper_2110_10749_gb300 as ssd
+    h = 1 / 8
+    p = Q.sphere_points(1.0, h)
+    P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
+    inner = ssd.krylov(1e-13, 300, 100, False, ssd.FP64, False)
+    prm = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=0.0, uinf=(0.0, 0.0, 1.0), delta=3 * h, theta=theta,
+                         tol_outer=1e-12, maxit_outer=80, outer_gmres=True, traction_mode=ssd.TRACTION_JOSEPH_TAO,
+                         radius=1.0, inner=inner)
+    ritz, H = ssd.ddm_spectrum(gpu_ctx, P, prm, 40)
+    assert H.shape[1] == ritz.size
+    ref = np.linalg.eigvals(H[:-1, :])
+    assert np.abs(np.sort_complex(ritz) - np.sort_complex(ref)).max() < 1e-9
+    o = S.ddm_solve(p, 3 * h, 1.0, kappa, 0.0, [0.0, 0.0, 1.0], theta, tol=1e-12, inner_tol=1e-13, outer="gmres",
+                    traction="jt", R=1.0, restart=100, arnoldi=40)
+    # the extreme (well separated) eigenvalues: the n = 1 and n = 2 modes
+    a = np.sort(ritz.real)[:8]
+    b = np.sort(o["ritz"].real)[:8]
+    assert np.abs(a - b).max() < 1e-7 * max(1.0, np.abs(b).max())
+    # n = 1: (1 - theta) - theta R^2 / (3 kappa), from the exterior Stokeslet
+    a1 = (1 - theta) - theta / (3 * kappa)
+    assert np.abs(a[:3] - a1).max() < 5e-3 * max(1.0, abs(a1))
+    P.release()
