@@ -183,6 +183,19 @@ def run_reference(args):
     return 0
 
 
+def combine_ranks(ms, pairs, dist, device):
+    """Whole-job figures: the slowest rank's time and the pairs of all ranks
+    (identity without a process group)."""
+    if dist is None:
+        return ms, pairs
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([pairs], device=device, dtype=torch.float64)
+    dist.all_reduce(pt)
+    return float(t.item()), float(pt.item())
+
+
 def run_ours(args):
     import torch
     import paper_2110_10749_gb300 as ssd
@@ -259,15 +272,7 @@ def run_ours(args):
     ctx.set_timing(False)
     stats = {k: ctx.kernel_stats(k, ssd.FP32C) for k in range(6)}
     pairs_total = sum(s["pairs"] for s in stats.values())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pt = torch.tensor([pairs_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(pt)
-        pairs_all = float(pt.item())
-    else:
-        pairs_all = pairs_total
+    total_ms, pairs_all = combine_ranks(total_ms, pairs_total, dist, dev)
     value = pairs_all / (total_ms / 1e3)
 
     # time-to-solution and FP32C-vs-FP64 errors per solve
@@ -342,6 +347,7 @@ def run_ours(args):
         e2e_ms += 1e3 * (time.perf_counter() - t0)
     ctx.set_timing(False)
     e2e_pairs = sum(ctx.kernel_stats(c, ssd.FP32C)["pairs"] for c in range(6))
+    e2e_ms, e2e_pairs = combine_ranks(e2e_ms, e2e_pairs, dist, dev)
     e2e = {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": 6 * 7 * n * 8, "d2h_bytes_per_step": 6 * 8 * n * 8,
            "note": "ssd_ddm_solve_host per solve: host->device copy of the points, layout build, "
