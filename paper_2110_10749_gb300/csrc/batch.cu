@@ -14,7 +14,6 @@
 namespace ssd {
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 constexpr int kSegBlock = 2048;   // elements per reduction block (within one system segment)
 constexpr int kMaxM = 256;        // Krylov dimension limit
 

@@ -109,8 +109,6 @@ __device__ __forceinline__ Dual dsqrt(Dual a) {
     return {r, a.d / (2.0 * r)};
 }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ double val(double a) { return a; }
-__device__ __forceinline__ double val(Dual a) { return a.v; }
 
 template <typename T, bool GRAD = true>
 __device__ void star_eval(const T *a, T x, T y, T z, T &P, T g[3]) {

@@ -12,7 +12,6 @@
 namespace ssd {
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------ vector kernels
 constexpr int kMaxRestart = 512;
