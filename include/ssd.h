@@ -257,7 +257,7 @@ typedef struct {
                       sweeps (outer_gmres = 0) each local solve starts from the previous
                       sweep's solution; ssd_darcy_solve / ssd_stokes_solve start from
                       the values already in their output array.  Ignored by the
-                      interface GMRES's sweeps. */
+                      interface GMRES's sweeps and by batched solves. */
 } ssd_krylov;
 
 /*
