@@ -1244,6 +1244,37 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
 }
 
 
+// Near (warp, 32-source chunk) count of each FP32C work item of a batch, as
+// item_cost_kernel does for a single surface (smoothing radius per surface).
+__global__ void batch_item_cost_kernel(const BItem *items, int64_t nitems, const Consts<float> *consts,
+                                       const float4 *cbox, int32_t *key) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nitems) return;
+    const BItem bi = items[it];
+    const float rfar2 = consts[bi.surf].rfar2;
+    constexpr int kWarps = kTPB32 / 32;
+    const int64_t c0 = bi.tbase / kChunk;
+    int cnt = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+        for (int k = 0; k < kTPT32; ++k) {
+            const int64_t cc = c0 + w + k * kWarps;
+            const float4 l = cbox[2 * cc], h = cbox[2 * cc + 1];
+            lo[0] = fminf(lo[0], l.x); lo[1] = fminf(lo[1], l.y); lo[2] = fminf(lo[2], l.z);
+            hi[0] = fmaxf(hi[0], h.x); hi[1] = fmaxf(hi[1], h.y); hi[2] = fmaxf(hi[2], h.z);
+        }
+        if (lo[0] > hi[0]) continue;
+        for (int64_t sc = bi.s_beg / kChunk; sc < bi.s_end / kChunk; ++sc) {
+            const float4 l = cbox[2 * sc], h = cbox[2 * sc + 1];
+            const float gx = fmaxf(0.f, fmaxf(l.x - hi[0], lo[0] - h.x));
+            const float gy = fmaxf(0.f, fmaxf(l.y - hi[1], lo[1] - h.y));
+            const float gz = fmaxf(0.f, fmaxf(l.z - hi[2], lo[2] - h.z));
+            cnt += (gx * gx + gy * gy + gz * gz < rfar2) ? 1 : 0;
+        }
+    }
+    key[it] = cnt;
+}
+
 int pair_batch_items(ssd_ctx *ctx, BatchLayout *B, cudaStream_t s) {
     const int ns = B->nsurf;
     for (int pr = 0; pr < 2; ++pr) {   // 0: FP32C, 1: FP64
@@ -1310,6 +1341,33 @@ int pair_batch_items(ssd_ctx *ctx, BatchLayout *B, cudaStream_t s) {
                            "consts copy"));
         // the host vectors go out of scope: wait for the copies
         SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "items sync"));
+        if (pr == 0 && ctx->lpt && !items.empty()) {
+            // FP32C items in decreasing order of near work, so that cheap far
+            // items fill the last wave; each item keeps its own partial slot
+            const int64_t ni = (int64_t)items.size();
+            void *kd = nullptr;
+            SSD_TRY(dev_alloc(ctx, sizeof(int32_t) * ni, &kd));
+            struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } rel{ctx, kd};
+            batch_item_cost_kernel<<<(unsigned)((ni + 255) / 256), 256, 0, s>>>(
+                reinterpret_cast<const BItem *>(bp + o_it), ni, reinterpret_cast<const Consts<float> *>(bp + o_c),
+                B->L.cbox, static_cast<int32_t *>(kd));
+            ctx->launches++;
+            SSD_TRY(launch_check(ctx, "batch item cost kernel"));
+            std::vector<int32_t> hk(ni);
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(hk.data(), kd, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, s),
+                               "key copy"));
+            SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "key sync"));
+            int32_t kmax = 0;
+            for (int64_t i = 0; i < ni; ++i) kmax = hk[i] > kmax ? hk[i] : kmax;
+            std::vector<int64_t> start(kmax + 2, 0);
+            for (int64_t i = 0; i < ni; ++i) start[kmax - hk[i] + 1]++;
+            for (int k = 1; k <= kmax + 1; ++k) start[k] += start[k - 1];
+            std::vector<BItem> sorted(ni);
+            for (int64_t i = 0; i < ni; ++i) sorted[start[kmax - hk[i]]++] = items[i];
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(bp + o_it, sorted.data(), sizeof(BItem) * ni,
+                                                    cudaMemcpyHostToDevice, s), "items copy"));
+            SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "items sync"));
+        }
     }
     return SSD_OK;
 }
