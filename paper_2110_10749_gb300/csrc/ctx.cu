@@ -485,7 +485,8 @@ int check_points(ssd_ctx *ctx, const ssd_points *pts) {
 
 void release_layout(ssd_ctx *ctx, Layout *L) {
     if (L->block) dev_free(ctx, L->block);
-    if (L->order32) dev_free(ctx, L->order32);
+    for (int k = 0; k < 2; ++k)
+        if (L->order32[k]) dev_free(ctx, L->order32[k]);
     *L = Layout();
 }
 
@@ -621,6 +622,10 @@ int ssd_ctx_create(ssd_ctx **out, int device) {
     }
     // tuning knob: 0 launches the FP32C grid in plain (tile, split) order
     if (const char *w = getenv("SSD_PAIR_LPT")) ctx->lpt = atoi(w) != 0;
+    if (const char *w = getenv("SSD_PAIR_WAVES64")) {
+        const int v = atoi(w);
+        if (v >= 1 && v <= 64) ctx->waves64 = v;
+    }
     *out = ctx;
     return SSD_OK;
 }

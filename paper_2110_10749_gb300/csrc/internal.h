@@ -52,10 +52,11 @@ struct Layout {
     void *block = nullptr;     // single allocation backing the arrays
     // launch order of the FP32C pair grid (prepared layouts only), cached for
     // the last (grid, rho_far delta) it was built for
+    // (slot 0: FP32C packed kernel, slot 1: FP64 generic kernel)
     bool order_ok = false;
-    int2 *order32 = nullptr;
-    int64_t order_nit = 0, order_chunk = 0;
-    float order_rfar2 = -1.f;
+    int2 *order32[2] = {nullptr, nullptr};
+    int64_t order_nit[2] = {0, 0}, order_chunk[2] = {0, 0};
+    float order_rfar2[2] = {-1.f, -1.f};
 };
 
 struct TimedLaunch {
@@ -75,7 +76,8 @@ struct ssd_ctx {
     int num_sms = 0;
     int occ32 = 1, occ64 = 1;  // resident CTAs per SM of the pair kernels
     int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
-    int lpt = 1;               // FP32C grid in near-first order on prepared layouts
+    int lpt = 1;               // pair grids in near-first order on prepared layouts
+    int waves64 = 8;           // FP64 grid: about this many waves of resident CTAs (tuned)
     std::string err;
     // caching device allocator: blocks are reused in stream order
     struct Block { void *p; size_t bytes; bool used; };

@@ -101,6 +101,7 @@ template <typename R> struct KArgs {
     const Consts<R> *consts;   // per surface
     int64_t rec_stride;        // density records per right-hand side
     int64_t part_stride;       // partial values per right-hand side
+    const int2 *order = nullptr;   // single-surface launch order: blockIdx.x -> (target tile, split)
 };
 
 // Smoothed radial factors k1 = s1/r, k2 = s2/r^3, k3 = s3/r^3, k4 = s4/r^5
@@ -252,13 +253,19 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         part_base = blockIdx.y * a.part_stride + NC * NSL * sf.pbase + (int64_t)it.split * NC * NSL * sf.n_pad - sf.poff;
         pstride = sf.n_pad;
     } else {
-        tbase = (int64_t)blockIdx.x * (TPB * TPT);
-        s_beg = (int64_t)blockIdx.y * a.chunk;
+        int64_t bt = blockIdx.x, bs = blockIdx.y;
+        if (a.order) {
+            const int2 o = a.order[blockIdx.x];
+            bt = o.x;
+            bs = o.y;
+        }
+        tbase = bt * (TPB * TPT);
+        s_beg = bs * a.chunk;
         s_end = s_beg + a.chunk;
         if (s_end > a.n_pad) s_end = a.n_pad;
         c = a.c;
         constexpr int NSL = sizeof(Acc<R>) / sizeof(R);
-        part_base = (int64_t)blockIdx.y * NC * NSL * a.n_pad;
+        part_base = bs * NC * NSL * a.n_pad;
         pstride = a.n_pad;
     }
     constexpr bool TR = (OP == OP_LDLT || OP == OP_SDLT);
@@ -1018,17 +1025,17 @@ __global__ void bepilogue_kernel(const BEpiArgs a) {
 // items fill the last wave (longest-processing-time-first).  key = number of
 // near (warp, chunk) pairs of the item.
 __global__ void item_cost_kernel(const float4 *cbox, int64_t ntiles_t, int64_t nsplit, int64_t chunk, int64_t n_pad,
-                                 float rfar2, int32_t *key) {
+                                 float rfar2, int tpb, int tpt, int32_t *key) {
     const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= ntiles_t * nsplit) return;
     const int64_t t = it % ntiles_t, sp = it / ntiles_t;
-    constexpr int kWarps = kTPB32 / 32;
-    const int64_t c0 = t * (kTPB32 * kTPT32 / kChunk);
+    const int nwarps = tpb / 32;
+    const int64_t c0 = t * ((int64_t)tpb * tpt / kChunk);
     int cnt = 0;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < nwarps; ++w) {
         float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
-        for (int k = 0; k < kTPT32; ++k) {
-            const int64_t cc = c0 + w + k * kWarps;
+        for (int k = 0; k < tpt; ++k) {
+            const int64_t cc = c0 + w + k * nwarps;
             const float4 l = cbox[2 * cc], h = cbox[2 * cc + 1];
             lo[0] = fminf(lo[0], l.x); lo[1] = fminf(lo[1], l.y); lo[2] = fminf(lo[2], l.z);
             hi[0] = fmaxf(hi[0], h.x); hi[1] = fmaxf(hi[1], h.y); hi[2] = fmaxf(hi[2], h.z);
@@ -1048,20 +1055,21 @@ __global__ void item_cost_kernel(const float4 *cbox, int64_t ntiles_t, int64_t n
 }
 
 // Builds (once per layout, delta and grid) the launch order of the FP32C grid.
-int item_order(ssd_ctx *ctx, const Layout &L, int64_t ntiles_t, int64_t nsplit, int64_t chunk, float rfar2,
-               const int2 **order, cudaStream_t s) {
+int item_order(ssd_ctx *ctx, const Layout &L, int slot, int tpb, int tpt, int64_t ntiles_t, int64_t nsplit,
+               int64_t chunk, float rfar2, const int2 **order, cudaStream_t s) {
     Layout &M = const_cast<Layout &>(L);
     const int64_t nit = ntiles_t * nsplit;
-    if (M.order32 && M.order_nit == nit && M.order_chunk == chunk && M.order_rfar2 == rfar2) {
-        *order = M.order32;
+    if (M.order32[slot] && M.order_nit[slot] == nit && M.order_chunk[slot] == chunk &&
+        M.order_rfar2[slot] == rfar2) {
+        *order = M.order32[slot];
         return SSD_OK;
     }
-    if (M.order32) { dev_free(ctx, M.order32); M.order32 = nullptr; }
+    if (M.order32[slot]) { dev_free(ctx, M.order32[slot]); M.order32[slot] = nullptr; }
     void *keys = nullptr;
     SSD_TRY(dev_alloc(ctx, sizeof(int32_t) * nit, &keys));
     struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } release{ctx, keys};
     item_cost_kernel<<<(unsigned)((nit + 255) / 256), 256, 0, s>>>(L.cbox, ntiles_t, nsplit, chunk, L.n_pad, rfar2,
-                                                                   static_cast<int32_t *>(keys));
+                                                                   tpb, tpt, static_cast<int32_t *>(keys));
     ctx->launches++;
     SSD_TRY(launch_check(ctx, "item cost kernel"));
     std::vector<int32_t> hk(nit);
@@ -1078,14 +1086,14 @@ int item_order(ssd_ctx *ctx, const Layout &L, int64_t ntiles_t, int64_t nsplit, 
     for (int64_t i = 0; i < nit; ++i) ho[start[kmax - hk[i]]++] = make_int2((int)(i % ntiles_t), (int)(i / ntiles_t));
     void *dev = nullptr;
     SSD_TRY(dev_alloc(ctx, sizeof(int2) * nit, &dev));
-    M.order32 = static_cast<int2 *>(dev);
-    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(M.order32, ho.data(), sizeof(int2) * nit, cudaMemcpyHostToDevice, s),
-                       "order copy"));
+    M.order32[slot] = static_cast<int2 *>(dev);
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(M.order32[slot], ho.data(), sizeof(int2) * nit, cudaMemcpyHostToDevice,
+                                            s), "order copy"));
     SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "order sync"));
-    M.order_nit = nit;
-    M.order_chunk = chunk;
-    M.order_rfar2 = rfar2;
-    *order = M.order32;
+    M.order_nit[slot] = nit;
+    M.order_chunk[slot] = chunk;
+    M.order_rfar2[slot] = rfar2;
+    *order = M.order32[slot];
     return SSD_OK;
 }
 
@@ -1115,7 +1123,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     // uneven cost of near and far target tiles evens out (FP32C: tuned on the
     // h = 1/32 sphere, where it reaches one 128-source tile per CTA)
     const int occ = packed32 ? ctx->occ32 : ctx->occ64;
-    int64_t want = (int64_t)ctx->num_sms * occ * (packed32 ? ctx->waves32 : 2);
+    int64_t want = (int64_t)ctx->num_sms * occ * (packed32 ? ctx->waves32 : ctx->waves64);
     int64_t nsplit = (want + ntiles_t - 1) / ntiles_t;
     if (nsplit < 1) nsplit = 1;
     if (nsplit > ntiles_s) nsplit = ntiles_s;
@@ -1206,7 +1214,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         dim3 g = grid;
         if (ctx->lpt && L.order_ok) {
             const int2 *ord = nullptr;
-            const int st = item_order(ctx, L, ntiles_t, nsplit, chunk, ka.c.rfar2, &ord, s);
+            const int st = item_order(ctx, L, 0, kTPB32, kTPT32, ntiles_t, nsplit, chunk, ka.c.rfar2, &ord, s);
             if (st != SSD_OK) return st;
             ka.order = ord;
             g = dim3((unsigned)(ntiles_t * nsplit), 1);
@@ -1221,7 +1229,16 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.c = make_consts<double>(pc.delta, kRhoFar64);
         ka.part = reinterpret_cast<double *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
-        e = transposed ? launch_transpose<double>(op, grid, ka, s) : launch_pair_op64(op, grid, ka, s);
+        dim3 g = grid;
+        if (ctx->lpt && L.order_ok) {
+            const int2 *ord = nullptr;
+            const int st = item_order(ctx, L, 1, kTPB64, kTPT64, ntiles_t, nsplit, chunk,
+                                      (float)ka.c.rfar2, &ord, s);
+            if (st != SSD_OK) return st;
+            ka.order = ord;
+            g = dim3((unsigned)(ntiles_t * nsplit), 1);
+        }
+        e = transposed ? launch_transpose<double>(op, g, ka, s) : launch_pair_op64(op, g, ka, s);
     }
     ctx->launches++;
     if (e != cudaSuccess) return cuda_check(ctx, e, "pair kernel launch");
