@@ -353,6 +353,23 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
 int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m,
                      int *m_out, double *ritz_re, double *ritz_im, double *H, ssd_stream stream);
 
+/*
+ * The host step of ssd_ddm_spectrum on its own: eigenvalues of an upper
+ * Hessenberg matrix by the double-shifted QR iteration (Francis shifts from
+ * the trailing 2 x 2 block, exceptional shifts every tenth sweep, deflation
+ * when a subdiagonal entry is negligible against its diagonal neighbours or
+ * by the Ahues-Tisseur test).  Lets a caller take the Ritz values of a
+ * leading block of the H that ssd_ddm_spectrum returns.
+ * h: host, column-major, n x n with leading dimension ldh >= n; entries below
+ * the subdiagonal are ignored; h is not modified.  wr, wi: host [n], the
+ * eigenvalues by diagonal position at deflation, a complex pair in adjacent
+ * entries with the positive imaginary part first.  Runs on the host only (no
+ * context, no device).  SSD_EINVAL: n outside 1..4096, ldh < n, NULL pointer
+ * or a non-finite entry; SSD_ENUMERIC: no convergence within 100 n sweeps.
+ */
+int ssd_hessenberg_eigenvalues(int n, const double *h /* host */, int ldh, double *wr /* host */,
+                               double *wi /* host */);
+
 /* ------------------------------------------------------ off-surface fields
  * Field values away from the surface from the boundary data of a D-N solve
  * (FP64, bare kernels; accurate for field points a few grid spacings from

@@ -5,7 +5,9 @@ coupled Stokes-Darcy problem (arXiv 2110.10749) on sm_103a.  This module only
 marshals arguments: every step of the computation runs in the CUDA library.
 PyTorch supplies device memory and the current stream.  Importing works
 without a GPU; every call that computes needs the built library and a GPU and
-raises if either is missing (there is no CPU fallback).
+raises if either is missing (there is no CPU fallback).  The one exception is
+hessenberg_eigenvalues, the spectrum's host step, which is host code of the
+library by design.
 
 Functions keep the C names without the ``ssd_`` prefix.  Arrays are
 structure-of-arrays float64 CUDA tensors: points and vector densities have
@@ -39,6 +41,7 @@ EXPORTS = [
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
     "ssd_darcy_pressure_field", "ssd_stokes_velocity_field", "ssd_ddm_spectrum",
+    "ssd_hessenberg_eigenvalues",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
 FUNC_DRAG, FUNC_FLUX = 0, 1
@@ -148,6 +151,7 @@ def lib():
         "ssd_ddm_spectrum": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(i), C.POINTER(d),
                              C.POINTER(d), C.POINTER(d), P],
         "ssd_stokes_velocity_field": [P, C.POINTER(CPoints), d, C.POINTER(d), P, P, i64, P, P, P],
+        "ssd_hessenberg_eigenvalues": [i, C.POINTER(d), i, C.POINTER(d), C.POINTER(d)],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
         "ssd_batch_apply": [P, C.POINTER(CBatch), i, i, d, d, d, P, P, P, i, P],
@@ -486,6 +490,23 @@ def ddm_spectrum(ctx, pts, prm, m=50):
     ritz = np.array(re[:k]) + 1j * np.array(im[:k])
     Hm = np.array(H[:]).reshape(m, m + 1).T[:k + 1, :k]
     return ritz, Hm
+
+
+def hessenberg_eigenvalues(H):
+    """Eigenvalues (complex numpy array, in the library's deflation order) of
+    the upper Hessenberg matrix H (n, n): the host QR step of ddm_spectrum,
+    e.g. on a leading block of its H.  Host only; needs the built library but
+    no GPU."""
+    A = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("expected a square matrix")
+    n = A.shape[0]
+    re = (C.c_double * max(n, 1))()
+    im = (C.c_double * max(n, 1))()
+    st = lib().ssd_hessenberg_eigenvalues(n, A.ctypes.data_as(C.POINTER(C.c_double)), n, re, im)
+    if st != SSD_OK:
+        raise SsdError(st, "ssd_hessenberg_eigenvalues: %s" % lib().ssd_status_string(st).decode())
+    return np.array(re[:n]) + 1j * np.array(im[:n])
 
 
 def darcy_pressure_field(ctx, pts, mu, kappa, q, p, targets, out=None):

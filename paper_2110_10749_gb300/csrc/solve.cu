@@ -806,9 +806,10 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
 // ------------------------------------------------- discrete iteration matrix
 // Eigenvalues of a real upper Hessenberg matrix a (n x n, column-major,
 // overwritten) by the implicitly double-shifted QR iteration: deflate at
-// negligible subdiagonal entries (absolute, neighbour-gap and, for windows
-// stuck on clustered eigenvalues, 1e-11 relative tests), read off 1x1 and
-// 2x2 blocks, otherwise
+// negligible subdiagonal entries (normwise against the neighbouring diagonal,
+// refined by the neighbour-gap test, and, for windows stuck on clustered
+// eigenvalues, 1e-11 relative after 30 sweeps), read off 1x1 and 2x2 blocks,
+// otherwise
 // chase a bulge started from the first column of (H - s1)(H - s2), s1, s2 the
 // eigenvalues of the trailing 2x2 block (ad hoc shifts every tenth step).
 // Only the active window is transformed (enough for eigenvalues).
@@ -823,18 +824,25 @@ static int hessenberg_eigenvalues(int n, double *a, double *wr, double *wi) {
     while (hi >= 0) {
         int l = hi;
         for (; l > 0; --l) {
-            double sc = fabs(A(l - 1, l - 1)) + fabs(A(l, l));
-            if (sc == 0.0) sc = anorm;
             const double h = fabs(A(l, l - 1));
-            if (h <= eps * sc) { A(l, l - 1) = 0.0; break; }
-            // the coupling is also negligible when the off-diagonal pair's
-            // product is small against the gap of the neighbouring diagonal
-            // entries (the test of Ahues and Tisseur)
-            const double ab = fmax(h, fabs(A(l - 1, l))), ba = fmin(h, fabs(A(l - 1, l)));
-            const double gap = fabs(A(l - 1, l - 1) - A(l, l));
-            const double aa = fmax(fabs(A(l, l)), gap), bb = fmin(fabs(A(l, l)), gap);
-            const double s2 = aa + ab;
-            if (ba * (ab / s2) <= fmax(1e-300, eps * (bb * (aa / s2)))) { A(l, l - 1) = 0.0; break; }
+            if (h <= 1e-300) { A(l, l - 1) = 0.0; break; }
+            double sc = fabs(A(l - 1, l - 1)) + fabs(A(l, l));
+            if (sc == 0.0) {
+                if (l >= 2) sc += fabs(A(l - 1, l - 2));
+                if (l + 1 <= hi) sc += fabs(A(l + 1, l));
+            }
+            if (sc == 0.0) sc = anorm;
+            // normwise negligible, and (the test of Ahues and Tisseur) the
+            // off-diagonal pair's product also small against the gap of the
+            // neighbouring diagonal entries, which keeps small eigenvalues of
+            // graded matrices accurate; a stricter test than the first alone
+            if (h <= eps * sc) {
+                const double ab = fmax(h, fabs(A(l - 1, l))), ba = fmin(h, fabs(A(l - 1, l)));
+                const double gap = fabs(A(l - 1, l - 1) - A(l, l));
+                const double aa = fmax(fabs(A(l, l)), gap), bb = fmin(fabs(A(l, l)), gap);
+                const double s2 = aa + ab;
+                if (ba * (ab / s2) <= fmax(1e-300, eps * (bb * (aa / s2)))) { A(l, l - 1) = 0.0; break; }
+            }
             // clustered eigenvalues can leave a window stuck at rounding level
             if (iter >= 30 && h <= 1e-11 * sc) { A(l, l - 1) = 0.0; break; }
         }
@@ -868,21 +876,41 @@ static int hessenberg_eigenvalues(int n, double *a, double *wr, double *wi) {
         }
         if (++total > 100 * n) return -1;
         ++iter;
-        double sh, tt;
+        // shifts s1, s2 (complex: s1r +- i s1i)
+        double s1r, s1i = 0.0, s2r, s2i = 0.0;
         if (iter % 10 == 0) {
             const double w = fabs(A(hi, hi - 1)) + fabs(A(hi - 1, hi - 2));
-            const double m1 = A(hi, hi) + 0.75 * w, m2 = A(hi, hi) - 0.4375 * w;
-            sh = m1 + m2;
-            tt = m1 * m2;
+            s1r = A(hi, hi) + 0.75 * w;
+            s2r = A(hi, hi) - 0.4375 * w;
         } else {
-            sh = A(hi - 1, hi - 1) + A(hi, hi);
-            tt = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);
+            // eigenvalues of the trailing 2x2 block; a real pair is replaced
+            // by the eigenvalue nearer A(hi, hi), taken twice
+            const double p = A(hi - 1, hi - 1), q = A(hi - 1, hi), r = A(hi, hi - 1), t = A(hi, hi);
+            const double m = 0.5 * (p + t), d = 0.5 * (p - t);
+            const double disc = d * d + q * r;
+            if (disc >= 0.0) {
+                const double sq = sqrt(disc);
+                const double e1 = m + sq, e2 = m - sq;
+                s1r = s2r = fabs(e1 - t) <= fabs(e2 - t) ? e1 : e2;
+            } else {
+                s1r = s2r = m;
+                s1i = sqrt(-disc);
+                s2i = -s1i;
+            }
         }
-        double x = A(l, l) * A(l, l) + A(l, l + 1) * A(l + 1, l) - sh * A(l, l) + tt;
-        double y = A(l + 1, l) * (A(l, l) + A(l + 1, l + 1) - sh);
-        double z = A(l + 1, l) * A(l + 2, l + 1);
+        // first column of (H - s1)(H - s2) in product form, scaled: no
+        // cancellation of O(|H|^2) terms when the spectrum is clustered
+        const double d1 = A(l, l) - s1r, d2 = A(l, l) - s2r;
+        const double sc = fabs(d2) + fabs(s2i) + fabs(A(l + 1, l));
+        const double h21 = A(l + 1, l) / sc;
+        double x = h21 * A(l, l + 1) + d1 * (d2 / sc) - s1i * (s2i / sc);
+        double y = h21 * (d1 + (A(l + 1, l + 1) - s2r));
+        double z = h21 * A(l + 2, l + 1);
         for (int k = l; k <= hi - 2; ++k) {
-            // reflector I - 2 v v^T / (v^T v) taking (x, y, z) to (alpha, 0, 0)
+            // reflector I - 2 v v^T / (v^T v) taking (x, y, z) to (alpha, 0, 0);
+            // (x, y, z) normalised first against over- and underflow
+            const double s3 = fabs(x) + fabs(y) + fabs(z);
+            if (s3 != 0.0) { x /= s3; y /= s3; z /= s3; }
             const double nv = sqrt(x * x + y * y + z * z);
             if (nv != 0.0) {
                 const double alpha = x >= 0.0 ? -nv : nv;
@@ -1593,6 +1621,24 @@ int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     return ddm_spectrum_impl(ctx, pts, prm, m, m_out, ritz_re, ritz_im, H, (cudaStream_t)stream);
+}
+
+int ssd_hessenberg_eigenvalues(int n, const double *h, int ldh, double *wr, double *wi) {
+    if (n < 1 || n > 4096 || ldh < n || !h || !wr || !wi) return SSD_EINVAL;
+    try {
+        std::vector<double> a((size_t)n * n, 0.0);     // entries below the subdiagonal start at 0
+        for (int j = 0; j < n; ++j) {
+            const int iend = j + 1 < n ? j + 1 : n - 1;
+            for (int i = 0; i <= iend; ++i) {
+                const double v = h[i + (size_t)j * ldh];
+                if (!isfinite(v)) return SSD_EINVAL;
+                a[i + (size_t)j * n] = v;
+            }
+        }
+        return hessenberg_eigenvalues(n, a.data(), wr, wi) == 0 ? SSD_OK : SSD_ENUMERIC;
+    } catch (...) {
+        return SSD_ENOMEM;
+    }
 }
 
 int ssd_ddm_gradient(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int functional, double *value,
