@@ -27,7 +27,11 @@
  * - Non-finite scalar arguments, n <= 0, delta <= 0, mu <= 0, kappa <= 0,
  *   theta outside (0,1] and NULL required pointers give SSD_EINVAL before any
  *   work is enqueued.
- * - A context is used by one host thread at a time.
+ * - A context is used by one host thread at a time.  Its workspace is a
+ *   cache of device blocks handed out again as soon as a call has enqueued
+ *   its work, so the work of one context must stay in one stream order: use
+ *   one stream per context, or order the streams yourself (an event from the
+ *   previous call's stream) before a call on another stream.
  */
 #ifndef SSD_H
 #define SSD_H
