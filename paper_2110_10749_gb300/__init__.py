@@ -440,23 +440,42 @@ def ddm_solve(ctx, pts, prm, raise_on_notconv=True):
     return o
 
 
+def _host_ptr(a, shape, writable=False):
+    """Pointer to a host float64 array of the given shape (numpy array or CPU
+    tensor, pinned for the fastest copies).  Inputs of another dtype or
+    layout are converted (the converted array is returned to keep it alive);
+    outputs must already be contiguous float64 of that shape."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError("expected a contiguous float64 CPU tensor of shape %s" % (tuple(shape),))
+        return C.c_void_p(a.data_ptr()), a
+    if writable:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                and a.flags.writeable and a.shape == tuple(shape)):
+            raise ValueError("output must be a writable C-contiguous float64 array of shape %s" % (tuple(shape),))
+    else:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != tuple(shape):
+            raise ValueError("expected shape %s, got %s" % (tuple(shape), a.shape))
+    return a.ctypes.data_as(C.c_void_p), a
+
+
 def ddm_solve_host(ctx, xyz, nrm, w, prm, out=None, raise_on_notconv=True):
     """D-N solve with host (numpy or pinned CPU tensor) buffers; copies happen inside."""
-    def hp(a):
-        if hasattr(a, "data_ptr"):
-            assert not a.is_cuda and a.is_contiguous()
-            return C.c_void_p(a.data_ptr())
-        a = np.ascontiguousarray(a, dtype=np.float64)
-        return a.ctypes.data_as(C.c_void_p)
     n = int(w.shape[0])
     out = out or {"q": np.empty(n), "p": np.empty(n), "u": np.empty((3, n)), "f": np.empty((3, n))}
+    keep = [_host_ptr(xyz, (3, n)), _host_ptr(nrm, (3, n)), _host_ptr(w, (n,))]
+    keep += [_host_ptr(out[k], sh, writable=True) for k, sh in (("q", (n,)), ("p", (n,)), ("u", (3, n)),
+                                                                 ("f", (3, n)))]
+    ptr = [k[0] for k in keep]
     drag = (C.c_double * 3)()
     oits = C.c_int()
     cap = 2 * (prm.maxit_outer + 2)
     inner = (C.c_int * cap)()
     hist = (C.c_double * max(prm.maxit_outer, 1))()
-    st = lib().ssd_ddm_solve_host(ctx.h, n, hp(xyz), hp(nrm), hp(w), C.byref(prm), hp(out["q"]), hp(out["p"]),
-                                  hp(out["u"]), hp(out["f"]), drag, C.byref(oits), inner, hist, _stream())
+    st = lib().ssd_ddm_solve_host(ctx.h, n, ptr[0], ptr[1], ptr[2], C.byref(prm), ptr[3], ptr[4], ptr[5], ptr[6],
+                                  drag, C.byref(oits), inner, hist, _stream())
     if st != SSD_ENOTCONV or raise_on_notconv:
         ctx.check(st, "ssd_ddm_solve_host")
     out["status"] = st

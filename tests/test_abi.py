@@ -63,3 +63,30 @@ def test_python_api_refuses_to_run_without_gpu():
     import paper_2110_10749_gb300 as ssd
     with pytest.raises(RuntimeError):
         ssd.Context(0)
+
+
+def test_host_buffer_marshalling():
+    """ddm_solve_host's host buffers: inputs are converted to contiguous
+    float64 (and kept alive), outputs must already be writable contiguous
+    float64 of the right shape, CPU tensors are taken as they are."""
+    import numpy as np
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    n = 5
+    a = np.arange(3 * n, dtype=np.float32).reshape(n, 3).T      # non-contiguous float32 input
+    p, keep = ssd._host_ptr(a, (3, n))
+    assert keep.dtype == np.float64 and keep.flags.c_contiguous and np.array_equal(keep, a)
+    assert p.value == keep.ctypes.data
+    with pytest.raises(ValueError):
+        ssd._host_ptr(np.zeros(n + 1), (n,))
+    out = np.empty((3, n))
+    p, keep = ssd._host_ptr(out, (3, n), writable=True)
+    assert keep is out and p.value == out.ctypes.data
+    for bad in (np.empty((3, n), dtype=np.float32), np.empty((n, 3)).T, np.empty(n)):
+        with pytest.raises(ValueError):
+            ssd._host_ptr(bad, (3, n), writable=True)
+    t = torch.zeros((3, n), dtype=torch.float64)
+    p, keep = ssd._host_ptr(t, (3, n), writable=True)
+    assert keep is t and p.value == t.data_ptr()
+    with pytest.raises(ValueError):
+        ssd._host_ptr(torch.zeros((3, n), dtype=torch.float32), (3, n))
