@@ -188,6 +188,28 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_arg(t, numel, device, what):
+    """The C calls read or write exactly `numel` elements of each device
+    array and cannot see a tensor's size: check it (and that the array sits
+    on the points' device) before passing the pointer."""
+    if t is None:
+        return
+    if t.numel() != numel:
+        raise ValueError("%s: expected %d elements, got %d (shape %s)" % (what, numel, t.numel(), tuple(t.shape)))
+    if device is not None and t.device != device:
+        raise ValueError("%s: on %s, the points are on %s" % (what, t.device, device))
+
+
+def _arg(t, numel, device, what):
+    _check_arg(t, numel, device, what)
+    return _ptr(t)
+
+
+def _nc(op):
+    """Components of an operator's densities (1 Laplace, 3 Stokes)."""
+    return 1 if op in (OP_LAPLACE_SL, OP_LAPLACE_DL, OP_LAPLACE_SLDL) else 3
+
+
 class Context:
     """Owns an ssd_ctx on one device."""
 
@@ -322,59 +344,70 @@ def _out_like(t, out):
 
 def laplace_SL(ctx, pts, delta, g, prec=FP64, out=None):
     out = _out_like(g, out)
-    ctx.check(lib().ssd_laplace_SL(ctx.h, C.byref(pts.c), float(delta), _ptr(g), _ptr(out), prec, _stream()),
-              "ssd_laplace_SL")
+    n, dv = pts.n, pts.xyz.device
+    ctx.check(lib().ssd_laplace_SL(ctx.h, C.byref(pts.c), float(delta), _arg(g, n, dv, "g"), _arg(out, n, dv, "out"),
+                                   prec, _stream()), "ssd_laplace_SL")
     return out
 
 
 def laplace_DL(ctx, pts, delta, p, prec=FP64, out=None):
     out = _out_like(p, out)
-    ctx.check(lib().ssd_laplace_DL(ctx.h, C.byref(pts.c), float(delta), _ptr(p), _ptr(out), prec, _stream()),
-              "ssd_laplace_DL")
+    n, dv = pts.n, pts.xyz.device
+    ctx.check(lib().ssd_laplace_DL(ctx.h, C.byref(pts.c), float(delta), _arg(p, n, dv, "p"), _arg(out, n, dv, "out"),
+                                   prec, _stream()), "ssd_laplace_DL")
     return out
 
 
 def stokes_SL(ctx, pts, delta, mu, f, prec=FP64, out=None):
     out = _out_like(f, out)
-    ctx.check(lib().ssd_stokes_SL(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), _ptr(out), prec,
-                                  _stream()), "ssd_stokes_SL")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_SL(ctx.h, C.byref(pts.c), float(delta), float(mu), _arg(f, n3, dv, "f"),
+                                  _arg(out, n3, dv, "out"), prec, _stream()), "ssd_stokes_SL")
     return out
 
 
 def stokes_DL(ctx, pts, delta, u, prec=FP64, out=None):
     out = _out_like(u, out)
-    ctx.check(lib().ssd_stokes_DL(ctx.h, C.byref(pts.c), float(delta), _ptr(u), _ptr(out), prec, _stream()),
-              "ssd_stokes_DL")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_DL(ctx.h, C.byref(pts.c), float(delta), _arg(u, n3, dv, "u"),
+                                  _arg(out, n3, dv, "out"), prec, _stream()), "ssd_stokes_DL")
     return out
 
 
 def apply_transpose(ctx, pts, op, delta, dens, mu=1.0, prec=FP64, out=None):
     """out = A^T dens for op in OP_LAPLACE_SL/DL, OP_STOKES_SL/DL (adjoint operators)."""
     out = _out_like(dens, out)
-    ctx.check(lib().ssd_apply_transpose(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu), _ptr(dens),
-                                        _ptr(out), int(prec), _stream()), "ssd_apply_transpose")
+    m, dv = _nc(op) * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_apply_transpose(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu),
+                                        _arg(dens, m, dv, "dens"), _arg(out, m, dv, "out"), int(prec), _stream()),
+              "ssd_apply_transpose")
     return out
 
 
 def stokes_DL_noalloc(ctx, pts, delta, u, out=None):
     """Stokes double layer in FP32C without device allocation (see include/ssd.h)."""
     out = _out_like(u, out)
-    ctx.check(lib().ssd_stokes_DL_noalloc(ctx.h, C.byref(pts.c), float(delta), _ptr(u), _ptr(out), _stream()),
-              "ssd_stokes_DL_noalloc")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_DL_noalloc(ctx.h, C.byref(pts.c), float(delta), _arg(u, n3, dv, "u"),
+                                          _arg(out, n3, dv, "out"), _stream()), "ssd_stokes_DL_noalloc")
     return out
 
 
 def stokes_SLDL(ctx, pts, delta, mu, f, u, alpha=1.0, beta=1.0, prec=FP64, out=None):
     out = _out_like(u, out)
-    ctx.check(lib().ssd_stokes_SLDL(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), _ptr(u),
-                                    float(alpha), float(beta), _ptr(out), prec, _stream()), "ssd_stokes_SLDL")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_SLDL(ctx.h, C.byref(pts.c), float(delta), float(mu), _arg(f, n3, dv, "f"),
+                                    _arg(u, n3, dv, "u"), float(alpha), float(beta), _arg(out, n3, dv, "out"), prec,
+                                    _stream()), "ssd_stokes_SLDL")
     return out
 
 
 def laplace_SLDL(ctx, pts, delta, g, p, alpha=1.0, beta=1.0, prec=FP64, out=None):
     out = _out_like(p, out)
-    ctx.check(lib().ssd_laplace_SLDL(ctx.h, C.byref(pts.c), float(delta), _ptr(g), _ptr(p), float(alpha),
-                                     float(beta), _ptr(out), prec, _stream()), "ssd_laplace_SLDL")
+    n, dv = pts.n, pts.xyz.device
+    ctx.check(lib().ssd_laplace_SLDL(ctx.h, C.byref(pts.c), float(delta), _arg(g, n, dv, "g"), _arg(p, n, dv, "p"),
+                                     float(alpha), float(beta), _arg(out, n, dv, "out"), prec, _stream()),
+              "ssd_laplace_SLDL")
     return out
 
 
@@ -387,8 +420,10 @@ def darcy_solve(ctx, pts, delta, mu, kappa, q, kr=None, out=None):
     kr = kr or krylov()
     out = _out_like(q, out)
     its, rel = C.c_int(), C.c_double()
-    ctx.check(lib().ssd_darcy_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), float(kappa), _ptr(q),
-                                    _ptr(out), C.byref(kr), C.byref(its), C.byref(rel), _stream()),
+    n, dv = pts.n, pts.xyz.device
+    ctx.check(lib().ssd_darcy_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), float(kappa),
+                                    _arg(q, n, dv, "q"), _arg(out, n, dv, "out"), C.byref(kr), C.byref(its),
+                                    C.byref(rel), _stream()),
               "ssd_darcy_solve")
     return out, its.value, rel.value
 
@@ -398,8 +433,10 @@ def stokes_solve(ctx, pts, delta, mu, f, uinf, kr=None, out=None):
     out = _out_like(f, out)
     its, rel = C.c_int(), C.c_double()
     ui = (C.c_double * 3)(*uinf)
-    ctx.check(lib().ssd_stokes_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), _ptr(f), ui, _ptr(out),
-                                     C.byref(kr), C.byref(its), C.byref(rel), _stream()), "ssd_stokes_solve")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_solve(ctx.h, C.byref(pts.c), float(delta), float(mu), _arg(f, n3, dv, "f"), ui,
+                                     _arg(out, n3, dv, "out"), C.byref(kr), C.byref(its), C.byref(rel), _stream()),
+              "ssd_stokes_solve")
     return out, its.value, rel.value
 
 
@@ -533,8 +570,10 @@ def darcy_pressure_field(ctx, pts, mu, kappa, q, p, targets, out=None):
     torch = _torch()
     nt = int(targets.shape[1])
     out = out if out is not None else torch.empty((nt,), dtype=torch.float64, device=targets.device)
-    ctx.check(lib().ssd_darcy_pressure_field(ctx.h, C.byref(pts.c), float(mu), float(kappa), _ptr(q), _ptr(p), nt,
-                                             _ptr(targets), _ptr(out), _stream()), "ssd_darcy_pressure_field")
+    n, dv = pts.n, pts.xyz.device
+    ctx.check(lib().ssd_darcy_pressure_field(ctx.h, C.byref(pts.c), float(mu), float(kappa), _arg(q, n, dv, "q"),
+                                             _arg(p, n, dv, "p"), nt, _arg(targets, 3 * nt, dv, "targets"),
+                                             _arg(out, nt, dv, "out"), _stream()), "ssd_darcy_pressure_field")
     return out
 
 
@@ -544,8 +583,10 @@ def stokes_velocity_field(ctx, pts, mu, uinf, f, u, targets, out=None):
     nt = int(targets.shape[1])
     out = out if out is not None else torch.empty((3, nt), dtype=torch.float64, device=targets.device)
     ui = (C.c_double * 3)(*uinf)
-    ctx.check(lib().ssd_stokes_velocity_field(ctx.h, C.byref(pts.c), float(mu), ui, _ptr(f), _ptr(u), nt,
-                                              _ptr(targets), _ptr(out), _stream()), "ssd_stokes_velocity_field")
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_velocity_field(ctx.h, C.byref(pts.c), float(mu), ui, _arg(f, n3, dv, "f"),
+                                              _arg(u, n3, dv, "u"), nt, _arg(targets, 3 * nt, dv, "targets"),
+                                              _arg(out, 3 * nt, dv, "out"), _stream()), "ssd_stokes_velocity_field")
     return out
 
 
@@ -557,8 +598,10 @@ def geometry_gradient(ctx, pts, op, delta, a, b, mu=1.0, alpha=1.0, out=None):
         dev = pts.xyz.device
         out = (torch.zeros((3, n), dtype=torch.float64, device=dev), torch.zeros((3, n), dtype=torch.float64,
                device=dev), torch.zeros((n,), dtype=torch.float64, device=dev))
+    m, dv = _nc(op) * n, pts.xyz.device
     ctx.check(lib().ssd_geometry_gradient(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu), float(alpha),
-                                          _ptr(a), _ptr(b), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream()),
+                                          _arg(a, m, dv, "a"), _arg(b, m, dv, "b"), _arg(out[0], 3 * n, dv, "gx"),
+                                          _arg(out[1], 3 * n, dv, "gn"), _arg(out[2], n, dv, "gw"), _stream()),
               "ssd_geometry_gradient")
     return out
 
@@ -584,8 +627,11 @@ def shape_contract(ctx, jac, geo):
     """dJ/dc_k from a quadrature Jacobian (dict) and geometry gradients (gx, gn, gw)."""
     ncoef, _, n = jac["dxyz"].shape
     out = (C.c_double * ncoef)()
-    ctx.check(lib().ssd_shape_contract(ctx.h, int(n), int(ncoef), _ptr(jac["dxyz"]), _ptr(jac["dnrm"]),
-                                       _ptr(jac["dw"]), _ptr(geo[0]), _ptr(geo[1]), _ptr(geo[2]), out, _stream()),
+    dv = jac["dxyz"].device
+    ctx.check(lib().ssd_shape_contract(ctx.h, int(n), int(ncoef), _arg(jac["dxyz"], 3 * ncoef * n, dv, "dxyz"),
+                                       _arg(jac["dnrm"], 3 * ncoef * n, dv, "dnrm"),
+                                       _arg(jac["dw"], ncoef * n, dv, "dw"), _arg(geo[0], 3 * n, dv, "gx"),
+                                       _arg(geo[1], 3 * n, dv, "gn"), _arg(geo[2], n, dv, "gw"), out, _stream()),
               "ssd_shape_contract")
     return np.array(out[:])
 
@@ -700,11 +746,13 @@ class Batch:
 def batch_apply(ctx, batch, op, dens0, dens1=None, mu=1.0, alpha=1.0, beta=1.0, prec=FP64, out=None):
     """One launch of `op` for every surface and right-hand side; densities [nrhs][c][n_total]."""
     nrhs = int(dens0.shape[0])
-    nc = 1 if op in (OP_LAPLACE_SL, OP_LAPLACE_DL, OP_LAPLACE_SLDL) else 3
+    nc = _nc(op)
     if out is None:
         out = _torch().empty((nrhs, nc, batch.n), dtype=_torch().float64, device=dens0.device)
+    m, dv = nrhs * nc * batch.n, batch.xyz.device
     ctx.check(lib().ssd_batch_apply(ctx.h, C.byref(batch.c), int(op), nrhs, float(mu), float(alpha), float(beta),
-                                    _ptr(dens0), _ptr(dens1), _ptr(out), int(prec), _stream()), "ssd_batch_apply")
+                                    _arg(dens0, m, dv, "dens0"), _arg(dens1, m, dv, "dens1"), _arg(out, m, dv, "out"),
+                                    int(prec), _stream()), "ssd_batch_apply")
     return out
 
 

@@ -90,3 +90,20 @@ def test_host_buffer_marshalling():
     assert keep is t and p.value == t.data_ptr()
     with pytest.raises(ValueError):
         ssd._host_ptr(torch.zeros((3, n), dtype=torch.float32), (3, n))
+
+
+def test_device_array_size_and_device_checks():
+    """The binding checks each device array's element count (the C calls
+    cannot) and its device before passing a pointer."""
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    cpu = torch.device("cpu")
+    ssd._check_arg(torch.zeros((3, 7)), 21, cpu, "u")
+    ssd._check_arg(torch.zeros(21), 21, cpu, "u")          # any shape with the right count
+    ssd._check_arg(None, 21, cpu, "optional")
+    with pytest.raises(ValueError, match="expected 21 elements"):
+        ssd._check_arg(torch.zeros((3, 6)), 21, cpu, "u")
+    with pytest.raises(ValueError, match="points are on"):
+        ssd._check_arg(torch.zeros(4), 4, torch.device("meta"), "g")
+    assert ssd._nc(ssd.OP_LAPLACE_DL) == 1 and ssd._nc(ssd.OP_LAPLACE_SLDL) == 1
+    assert ssd._nc(ssd.OP_STOKES_SL) == 3 and ssd._nc(ssd.OP_STOKES_SLDL) == 3
