@@ -266,7 +266,10 @@ class Points:
         self.nrm = nrm.to(dtype=torch.float64).contiguous()
         self.w = w.to(dtype=torch.float64).contiguous()
         self.n = int(self.w.numel())
-        assert self.xyz.shape == (3, self.n) and self.nrm.shape == (3, self.n)
+        if self.xyz.shape != (3, self.n) or self.nrm.shape != (3, self.n):
+            raise ValueError("xyz and nrm must have shape (3, n) with n = w.numel()")
+        if self.xyz.device != self.w.device or self.nrm.device != self.w.device:
+            raise ValueError("xyz, nrm and w must be on one device")
         self.c = CPoints(self.n, _ptr(self.xyz), _ptr(self.nrm), _ptr(self.w), None)
         self.ctx = None
 
@@ -720,7 +723,10 @@ class Batch:
         self.delta = (C.c_double * len(delta))(*[float(v) for v in delta])
         self.nsurf = len(delta)
         self.n = int(self.w.numel())
-        assert len(offsets) == self.nsurf + 1 and int(offsets[-1]) == self.n
+        if len(offsets) != self.nsurf + 1 or int(offsets[-1]) != self.n:
+            raise ValueError("offsets must have nsurf + 1 entries ending at n_total")
+        if self.xyz.shape != (3, self.n) or self.nrm.shape != (3, self.n):
+            raise ValueError("xyz and nrm must have shape (3, n_total)")
         self.c = CBatch(self.nsurf, self.offsets, self.delta, _ptr(self.xyz), _ptr(self.nrm), _ptr(self.w), None)
         self.ctx = None
 
