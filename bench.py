@@ -154,6 +154,18 @@ def oracle_pair_rate(budget_s, xyz, nrm, w, delta):
                                   % (calls, rows.size, n)}
 
 
+def oracle_single_thread_rate(budget_s, xyz, nrm, w, delta):
+    """The same sampled oracle work on one OpenMP thread (thread count restored after)."""
+    import oracle
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        rate, info = oracle_pair_rate(budget_s, xyz, nrm, w, delta)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": rate, "cores": info["cores"], "sample": info["sample"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -355,8 +367,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
-        rate, info = oracle_pair_rate(args.cpu_seconds, xyz_h, q["nrm"].cpu().numpy(), q["w"].cpu().numpy(), 3 * H)
-        cpu = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+        nrm_h, w_h = q["nrm"].cpu().numpy(), q["w"].cpu().numpy()
+        rate, info = oracle_pair_rate(args.cpu_seconds, xyz_h, nrm_h, w_h, 3 * H)
+        cpu = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
+               "single_thread": oracle_single_thread_rate(0.25 * args.cpu_seconds, xyz_h, nrm_h, w_h, 3 * H)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

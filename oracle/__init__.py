@@ -69,6 +69,8 @@ def lib():
             L.ssdo_stokes_sl.argtypes = [i64, P, i64, P, P, d, d, P, P]
             L.ssdo_stokes_dl.argtypes = [i64, P, P, P, d, P, i64, P, P]
             L.ssdo_num_threads.restype = i32
+            L.ssdo_set_threads.argtypes = [i32]
+            L.ssdo_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -95,6 +97,11 @@ def sigma(i: int, rho: float) -> float:
 
 def num_threads() -> int:
     return int(lib().ssdo_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    """Thread count of the oracle's OpenMP loops (for baseline timings)."""
+    lib().ssdo_set_threads(int(t))
 
 
 def laplace_sl(pts, delta, g, targets=None):

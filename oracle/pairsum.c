@@ -235,3 +235,14 @@ int ssdo_num_threads(void) {
     }
     return t;
 }
+
+/* Sets the OpenMP thread count of the oracle's loops, for the baseline's
+ * single-thread and all-core timings (t <= 0 leaves it unchanged). */
+void ssdo_set_threads(int t) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
