@@ -107,3 +107,23 @@ def test_device_array_size_and_device_checks():
         ssd._check_arg(torch.zeros(4), 4, torch.device("meta"), "g")
     assert ssd._nc(ssd.OP_LAPLACE_DL) == 1 and ssd._nc(ssd.OP_LAPLACE_SLDL) == 1
     assert ssd._nc(ssd.OP_STOKES_SL) == 3 and ssd._nc(ssd.OP_STOKES_SLDL) == 3
+
+
+def test_status_strings_and_null_handles(lib):
+    """Host-only entry points: every status code has its text, unknown codes
+    a fallback; NULL handles are refused (or accepted where documented)."""
+    import paper_2110_10749_gb300 as ssd
+    texts = {ssd.SSD_OK: b"ok", ssd.SSD_EINVAL: b"invalid argument", ssd.SSD_ENOMEM: b"out of memory",
+             ssd.SSD_ECUDA: b"CUDA error", ssd.SSD_ENOTCONV: b"iteration limit reached",
+             ssd.SSD_ENUMERIC: b"non-finite value"}
+    for st, text in texts.items():
+        assert lib.ssd_status_string(st) == text
+    assert lib.ssd_status_string(99) == b"unknown status"
+    assert lib.ssd_status_string(-1) == b"unknown status"
+    assert lib.ssd_ctx_last_error(None) == b""
+    assert lib.ssd_ctx_create(None, 0) == ssd.SSD_EINVAL
+    n = ctypes.c_int64()
+    assert lib.ssd_ctx_launch_count(None, ctypes.byref(n)) == ssd.SSD_EINVAL
+    assert lib.ssd_ctx_reset_stats(None) == ssd.SSD_EINVAL
+    assert lib.ssd_points_release(None, None) == ssd.SSD_EINVAL
+    assert lib.ssd_batch_release(None, None) == ssd.SSD_EINVAL
