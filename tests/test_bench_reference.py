@@ -40,3 +40,19 @@ def test_reference_arm_other_ranks_exit_silently():
     r = _run({"RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_near_fraction_sample_matches_the_full_count():
+    """The roofline's far/near flop weighting uses a sampled near-pair
+    fraction; on the h = 1/16 sphere it agrees with the count over all
+    ordered pairs."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import quadrature as Q
+    h = 1 / 16
+    xyz = Q.sphere_points(1.0, h)["xyz"]
+    n = xyz.shape[1]
+    r2 = (bench.RHO_FAR * 3 * h) ** 2
+    full = sum(int((((xyz[:, i:i + 512, None] - xyz[:, None, :]) ** 2).sum(0) < r2).sum())
+               for i in range(0, n, 512)) / n / n
+    assert abs(bench.near_fraction(xyz, 3 * h) - full) < 0.1 * full
