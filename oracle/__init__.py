@@ -12,13 +12,16 @@ pairsum.c      smoothing factors s_1..s_4 and the four layer operators as
 quadrature.py  quadrature points and weights (Section 5.4, eq. Quadrature).
 solvers.py     GMRES, successive approximations, Darcy and Stokes solves,
                the Dirichlet-Neumann iteration (Sections 3 and 6).
-analytic.py    Joseph-Tao porous-sphere solution, drag, spectrum (Sections 4, 7.3).
+analytic.py    Joseph-Tao porous-sphere solution, drag, spectrum (Sections 4, 7.3);
+               the porous sphere with Beavers-Joseph-Saffman slip (derived).
 field.py       off-surface Darcy pressure and Stokes velocity (eqs. Greens, Stokes).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests
-(closed forms, identities, printed table values); none is "parity unpinned"
-except where ``solvers.ddm_solve`` runs in BJS mode (no printed value exists;
-pinned only by h-convergence and internal consistency).
+(closed forms, identities, printed table values); none is "parity unpinned".
+The BJS mode of ``solvers.ddm_solve`` (no printed value exists) is pinned by
+the porous sphere with slip, a closed form derived in ``analytic.py`` and
+itself checked symbolically against the Stokes equations and the interface
+conditions; the opposite slip sign gives a different drag and field.
 """
 from __future__ import annotations
 
