@@ -71,6 +71,8 @@ def lib():
             L.ssdo_laplace_dl.argtypes = [i64, P, P, P, d, P, i64, P, P]
             L.ssdo_stokes_sl.argtypes = [i64, P, i64, P, P, d, d, P, P]
             L.ssdo_stokes_dl.argtypes = [i64, P, P, P, d, P, i64, P, P]
+            L.ssdo_operator_matrix.argtypes = [i32, i64, P, P, P, d, d, P]
+            L.ssdo_operator_matrix.restype = None
             L.ssdo_num_threads.restype = i32
             L.ssdo_set_threads.argtypes = [i32]
             L.ssdo_set_threads.restype = None
@@ -171,4 +173,17 @@ def stokes_dl(pts, delta, u, rows=None):
     out = np.empty((3, nr if rows is not None else n))
     lib().ssdo_stokes_dl(n, xyz[1], n_[1], w[1], float(delta), u[1], nr, pr,
                          out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def operator_matrix(pts, delta, op, mu=1.0):
+    """Dense matrix of L, D^L, M or D^S (op = "L", "DL", "M", "DS"), acting on
+    densities in the component-major order [3][n] -> 3n of the operators above."""
+    code = {"L": 0, "DL": 1, "M": 2, "DS": 3}[op]
+    xyz, n_, w = _c(pts["xyz"]), _c(pts["nrm"]), _c(pts["w"])
+    n = xyz[0].shape[1]
+    m = (3 if code >= 2 else 1) * n
+    out = np.empty((m, m))
+    lib().ssdo_operator_matrix(code, n, xyz[1], n_[1], w[1], float(delta), float(mu),
+                               out.ctypes.data_as(ctypes.c_void_p))
     return out

@@ -220,6 +220,58 @@ void ssdo_stokes_dl(int64_t n, const double *xyz, const double *nrm, const doubl
     }
 }
 
+/*
+ * Dense matrix of one operator (for the discrete iteration matrix of eq.
+ * A_mat, Section 6): out is (nc n) x (nc n), row-major, with the densities and
+ * results in the component-major order of the functions above (entry (a, i)
+ * at a n + i).  op: 0 = L, 1 = D^L, 2 = M, 3 = D^S.  Entry by entry the same
+ * kernels as the matrix-free loops; the subtraction of the double layers
+ * puts minus the row's off-diagonal sum on the diagonal (block).
+ */
+void ssdo_operator_matrix(int op, int64_t n, const double *xyz, const double *nrm, const double *w,
+                          double delta, double mu, double *out) {
+    int nc = (op >= 2) ? 3 : 1;
+    int64_t m = nc * n;
+    double d3 = delta * delta * delta, d5 = d3 * delta * delta;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double y0 = xyz[i], y1 = xyz[n + i], y2 = xyz[2 * n + i];
+        double diag[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3] = {y0 - xyz[j], y1 - xyz[n + j], y2 - xyz[2 * n + j]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double rho = r / delta;
+            double yn = d[0] * nrm[j] + d[1] * nrm[n + j] + d[2] * nrm[2 * n + j];
+            if (op == 0) {
+                out[i * m + j] = w[j] * (-ssdo_sigma(1, rho) / (4.0 * PI_D * delta));
+            } else if (op == 1) {
+                double K = w[j] * (-yn * ssdo_sigma(2, rho) / (4.0 * PI_D * d3));
+                out[i * m + j] = K;
+                diag[0][0] -= K;
+            } else if (op == 2) {
+                double c1 = ssdo_sigma(1, rho) / delta, c3 = ssdo_sigma(3, rho) / d3;
+                double s = w[j] / (8.0 * PI_D * mu);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        out[(a * n + i) * m + b * n + j] = s * ((a == b ? c1 : 0.0) + c3 * d[a] * d[b]);
+            } else {
+                double T = -6.0 * ssdo_sigma(4, rho) / d5;
+                double c = -(1.0 / (8.0 * PI_D)) * w[j] * T * yn;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        double v = c * d[a] * d[b];    /* row component a, density component b */
+                        out[(a * n + i) * m + b * n + j] = v;
+                        diag[a][b] -= v;
+                    }
+            }
+        }
+        if (op == 1) out[i * m + i] += diag[0][0];
+        if (op == 3)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) out[(a * n + i) * m + b * n + i] += diag[a][b];
+    }
+}
+
 /* Number of OpenMP threads the oracle's loops run on (reported by the baseline). */
 int ssdo_num_threads(void) {
     int t = 1;

@@ -317,6 +317,41 @@ def ddm_solve(pts, delta, mu, kappa, gamma, uinf, theta, tol=1e-9, maxit=100,
             "inner_its": inner_its, "hist": hist}
 
 
+def iteration_matrix(pts, delta, mu, kappa, theta, deflate=False):
+    """The discrete iteration matrix of the D-N sweeps (eq. A_mat, Section 6),
+    assembled from the dense operator matrices:
+
+        A~ = (1 - theta) I + theta N^T (I - D^S)^{-1} M N G,
+        G  = (mu/kappa) P0 (-D^L + 1 w^T / W)^{-1} L,
+
+    with N p = p n (so f = -p n and b_S = M N p for u_inf = 0, gamma = 0), N^T u
+    = u . n, P0 = I - 1 w^T / W the projection to zero weighted mean.  G is the
+    Darcy solve with the gauge of darcy_solve: the printed (I/2 - H~)^{-1} does
+    not exist (constants are in the kernel of D^L = H - I/2).  The signs are
+    those of eq. q_update with n the body normal (q = u . n); eq. A_mat writes
+    the same matrix as I - theta {I + (mu/kappa) [...] . n_S [...]}.
+    deflate: the Stokes matrix carries the rank-one normal-mode term
+    n (w . (u . n)) / W of stokes_solve.  Returns A~ (n x n).
+    """
+    n = pts["nrm"]
+    N = n.shape[1]
+    w = pts["w"]
+    W = float(w.sum())
+    L = oracle.operator_matrix(pts, delta, "L")
+    DL = oracle.operator_matrix(pts, delta, "DL")
+    M = oracle.operator_matrix(pts, delta, "M", mu)
+    DS = oracle.operator_matrix(pts, delta, "DS")
+    one = np.ones(N)
+    Gd = np.linalg.solve(-DL + np.outer(one, w) / W, (mu / kappa) * L)
+    Gd -= np.outer(one, w @ Gd) / W
+    Nm = np.concatenate([np.diag(n[0]), np.diag(n[1]), np.diag(n[2])])      # 3N x N
+    S = np.eye(3 * N) - DS
+    if deflate:
+        S += np.outer(n.ravel(), (w[None, :] * n).ravel()) / W
+    U = np.linalg.solve(S, M @ (Nm @ Gd))
+    return (1.0 - theta) * np.eye(N) + theta * (Nm.T @ U)
+
+
 def rms(v):
     """Unweighted RMS over points (eqs. error_Darcy, error_Stokes): v is [N] or [3][N]."""
     v = np.asarray(v)
