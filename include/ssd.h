@@ -319,17 +319,39 @@ typedef struct {
  * outer_gmres = 0: sweeps until ||q_k - q_{k-1}|| <= tol ||q_k|| (eq. DDM_residual).
  * outer_gmres = 1: GMRES on the affine interface map z -> G z + c,
  *   z = q (JOSEPH_TAO mode, gamma = 0, or bjs_implicit) or z = (q, u_prev) (lagged BJS),
+ *   solving D (I - G) z = D c where D divides the q rows of the stacked form
+ *   by theta (the unrelaxed map: theta (q - u.n) / theta; D = I for z = q),
  *   then one sweep from the solution gives the returned fields.
  * Outputs (device): q[n], p_D[n], u_S[3][n], f_S[3][n] (any may be NULL).
  * Host outputs: drag[3] = sum_x w f (eq. drag_int), *outer_its,
  *   inner_its[2 * max(maxit_outer + 2, 1)] = (Darcy, Stokes) iterations per sweep,
- *   res_hist[maxit_outer] = DDM residual per sweep (SA) or the final
- *   interface residual (GMRES, res_hist[0]).  Host pointers may be NULL.
+ *   res_hist[maxit_outer] = DDM residual per sweep (SA) or the interface
+ *   GMRES residual estimate ||D (c - (I - G) z_k)|| / ||D c|| after each step k
+ *   (GMRES; one cycle of up to min(maxit_outer, 512) steps, then restarts).
+ *   Host pointers may be NULL.
  * Synchronises `stream`.
  */
 int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
                   double *q, double *p_D, double *u_S, double *f_S, double drag[3],
                   int *outer_its, int *inner_its, double *res_hist, ssd_stream stream);
+
+/*
+ * One Dirichlet-Neumann sweep (Section 3, steps 1-3; Section 6, steps
+ * (a)-(f)) from the interface state (q, u_prev): b_D = (mu/kappa) L q, Darcy
+ * solve for p_D, traction f from p_D (and u_prev: the lagged slip of BJS mode
+ * with bjs_implicit = 0; ignored otherwise), b_S = U_inf - M f, Stokes solve
+ * for u_S, q_out = (1 - theta) q + theta u_S . n.  Local solves start from 0
+ * (prm->inner.warm is ignored); prm->outer_gmres, tol_outer and maxit_outer
+ * are ignored.  At a fixed point of the sweep, (q_out, u_S) = (q, u_prev).
+ * Device arrays: q[n] and q_out[n] (required, may not overlap), u_prev[3][n]
+ * (NULL = zero), outputs p_D[n], u_S[3][n], f_S[3][n] (any may be NULL).
+ * inner_its[2] (host, may be NULL) = (Darcy, Stokes) GMRES steps.
+ * Returns SSD_ENOTCONV (outputs filled) when a local solve reached its
+ * limit.  Synchronises `stream`.
+ */
+int ssd_ddm_sweep(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
+                  const double *q, const double *u_prev, double *q_out, double *p_D,
+                  double *u_S, double *f_S, int inner_its[2], ssd_stream stream);
 
 /*
  * Same solve with HOST buffers: copies xyz[3][n], nrm[3][n], w[n] to the

@@ -36,7 +36,7 @@ EXPORTS = [
     "ssd_quadrature_points", "ssd_quadrature_jacobian", "ssd_points_prepare", "ssd_points_release",
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
     "ssd_stokes_SLDL", "ssd_laplace_SLDL",
-    "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host",
+    "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host", "ssd_ddm_sweep",
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
@@ -140,6 +140,7 @@ def lib():
                           C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
         "ssd_ddm_solve_host": [P, i64, P, P, P, C.POINTER(CDdmParams), P, P, P, P, C.POINTER(d),
                                C.POINTER(i), C.POINTER(i), C.POINTER(d), P],
+        "ssd_ddm_sweep": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), P, P, P, P, P, P, C.POINTER(i), P],
         "ssd_stokes_DL_noalloc": [P, C.POINTER(CPoints), d, P, P, P],
         "ssd_apply_transpose": [P, C.POINTER(CPoints), i, d, d, P, P, i, P],
         "ssd_ddm_gradient": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(d), C.POINTER(d), P],
@@ -475,7 +476,24 @@ def ddm_solve(ctx, pts, prm, raise_on_notconv=True):
     o["outer_its"] = oits.value
     n_sweeps = oits.value + 2 if prm.outer_gmres else oits.value
     o["inner_its"] = [(inner[2 * k], inner[2 * k + 1]) for k in range(min(n_sweeps, cap // 2))]
-    o["hist"] = list(hist[:oits.value if not prm.outer_gmres else 1])
+    o["hist"] = list(hist[:min(oits.value, prm.maxit_outer)])
+    o["status"] = st
+    return o
+
+
+def ddm_sweep(ctx, pts, prm, q, u_prev=None, out=None, raise_on_notconv=True):
+    """One D-N sweep from (q, u_prev): dict with q (the relaxed update), p, u, f,
+    inner_its (Darcy, Stokes) and status."""
+    n, dv = pts.n, pts.xyz.device
+    o = out or _ddm_out(prm, n, dv)
+    its = (C.c_int * 2)()
+    st = lib().ssd_ddm_sweep(ctx.h, C.byref(pts.c), C.byref(prm), _arg(q, n, dv, "q"),
+                             _arg(u_prev, 3 * n, dv, "u_prev"), _arg(o["q"], n, dv, "q_out"),
+                             _arg(o["p"], n, dv, "p"), _arg(o["u"], 3 * n, dv, "u"), _arg(o["f"], 3 * n, dv, "f"),
+                             its, _stream())
+    if st != SSD_ENOTCONV or raise_on_notconv:
+        ctx.check(st, "ssd_ddm_sweep")
+    o["inner_its"] = (its[0], its[1])
     o["status"] = st
     return o
 

@@ -337,8 +337,10 @@ struct GmresResult {
 // (re)orthogonalisation pass when the DGKS test calls for it, x0 = 0 unless
 // `warm`.  Stops when the residual
 // estimate falls to tol * ||b|| or after maxit Arnoldi steps.
+// `trace`, when given, receives the residual estimate of every step read.
 int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double *b, double *x, double tol,
-          int restart, int maxit, bool warm, GmresResult *res, bool pipeline = true) {
+          int restart, int maxit, bool warm, GmresResult *res, bool pipeline = true,
+          std::vector<double> *trace = nullptr) {
     const int m = restart;
     // residual estimates come back through a pinned frame: with `pipeline`
     // the next Arnoldi step is queued before the previous one's residual is
@@ -435,6 +437,7 @@ int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double
                 SSD_TRY(fetch(pending));
                 rel = hb[0] / bnorm;
                 res->relres = rel;
+                if (trace) trace->push_back(rel);
                 if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
                 if (rel <= tol || hb[1] == 0.0) {
                     k = pending + 1;      // discard step j
@@ -454,6 +457,7 @@ int gmres(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A, const double
             k = j + 1;
             rel = hb[0] / bnorm;
             res->relres = rel;
+            if (trace) trace->push_back(rel);
             if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite residual");
             if (rel <= tol || total >= maxit || hb[1] == 0.0) { done = true; break; }
             prev_rel = rel;
@@ -749,11 +753,24 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
         }
         if (its > prm->maxit_outer) { its = prm->maxit_outer; status = SSD_ENOTCONV; }
     } else {
-        // GMRES on (I - G) z = c, c = F(0)
+        // GMRES on D (I - G) z = D c, c = F(0).  In the stacked (lagged BJS)
+        // form D divides the q rows, theta (q - u.n), by theta: the operator is
+        // then the unrelaxed interface map, independent of theta, and the q
+        // block (of size O(kappa)) is not swamped by the u block's residual.
+        // With z = q alone D = I (a global scale would not change GMRES).
         SSD_TRY(c.alloc(ctx, sizeof(double) * 4 * n));
         SSD_TRY(D.sweep(z.d(), z.d() + n, c.d(), c.d() + n, p.d()));
+        const double qscale = stacked ? 1.0 / prm->theta : 1.0;
+        Buf cs;
+        SSD_TRY(cs.alloc(ctx, sizeof(double) * 4 * n));
+        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(cs.d(), c.d(), sizeof(double) * nz, cudaMemcpyDeviceToDevice, s),
+                           "copy"));
+        if (stacked) {
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 0.0, cs.d(), qscale, cs.d());   // D c
+            ctx->launches++;
+        }
         auto F = [&](const double *v, double *out) -> int {
-            // out = v - (F(v) - c); F(v) = (q_new, u) of one sweep from v
+            // out = D (v - (F(v) - c)); F(v) = (q_new, u) of one sweep from v
             const double *uprev = stacked ? v + n : z.d() + n;   // z + n stays zero here
             SSD_TRY(D.sweep(v, uprev, zn.d(), zn.d() + n, p.d()));
             SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(out, c.d(), sizeof(double) * nz, cudaMemcpyDeviceToDevice, s),
@@ -761,16 +778,22 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
             axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, -1.0, zn.d(), 1.0, out);  // c - F(v)
             axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, 1.0, v, 1.0, out);        // + v
             ctx->launches += 2;
+            if (stacked) {
+                axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 0.0, out, qscale, out);
+                ctx->launches++;
+            }
             return launch_check(ctx, "outer matvec");
         };
         GmresResult gr;
-        const int m_out = prm->maxit_outer < 128 ? prm->maxit_outer : 128;
+        // the lagged BJS interface needs a few hundred steps at small kappa and
+        // large gamma; a restart there stalls, so the cycle is as long as allowed
+        const int m_out = prm->maxit_outer < kMaxRestart ? prm->maxit_outer : kMaxRestart;
         // each matvec is a whole sweep: no step is queued ahead of its check
-        int st = gmres(ctx, s, nz, F, c.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr, false);
+        int st = gmres(ctx, s, nz, F, cs.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr, false,
+                       &hist);
         if (st == SSD_ENOTCONV) status = SSD_ENOTCONV;
         else SSD_TRY(st);
         its = gr.iters;
-        hist.push_back(gr.relres);
         if (!stacked) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(z.d() + n, 0, sizeof(double) * 3 * n, s), "memset"));
         // final sweep from the solution gives the returned fields
         SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
@@ -801,6 +824,37 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     if (D.nonconv && status == SSD_OK) status = SSD_ENOTCONV;
     if (status == SSD_ENOTCONV) set_error(ctx, SSD_ENOTCONV, "iteration limit reached in the D-N solve");
     return status;
+}
+
+// One D-N sweep from a given interface state (q, u_prev).
+int ddm_sweep_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, const double *q,
+                   const double *u_prev, double *q_out, double *p_out, double *u_out, double *f_out,
+                   int *inner_its, cudaStream_t s) {
+    SSD_TRY(check_ddm(ctx, prm));
+    if (!q || !q_out) return set_error(ctx, SSD_EINVAL, "q and q_out are required");
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    Ddm D;
+    D.ctx = ctx; D.pts = pts; D.L = lref.L; D.P = *prm; D.P.outer_gmres = 1; D.s = s; D.n = pts->n;
+    const int64_t n = pts->n;
+    SSD_TRY(D.f.alloc(ctx, sizeof(double) * 3 * n));
+    Buf pb, ub, zb;
+    double *p = p_out, *u = u_out;
+    if (!p) { SSD_TRY(pb.alloc(ctx, sizeof(double) * n)); p = pb.d(); }
+    if (!u) { SSD_TRY(ub.alloc(ctx, sizeof(double) * 3 * n)); u = ub.d(); }
+    const double *up = u_prev;
+    if (!up) {
+        SSD_TRY(zb.alloc(ctx, sizeof(double) * 3 * n));
+        SSD_TRY(cuda_check(ctx, cudaMemsetAsync(zb.d(), 0, sizeof(double) * 3 * n, s), "memset"));
+        up = zb.d();
+    }
+    SSD_TRY(D.sweep(q, up, q_out, u, p));
+    if (f_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(f_out, D.f.d(), sizeof(double) * 3 * n,
+                                                       cudaMemcpyDeviceToDevice, s), "copy"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "sweep sync"));
+    if (inner_its && D.inner.size() >= 2) { inner_its[0] = D.inner[0]; inner_its[1] = D.inner[1]; }
+    if (D.nonconv) return set_error(ctx, SSD_ENOTCONV, "a local solve reached its iteration limit");
+    return SSD_OK;
 }
 
 // ------------------------------------------------- discrete iteration matrix
@@ -1614,6 +1668,14 @@ int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     return ddm_impl(ctx, pts, prm, q, p_D, u_S, f_S, drag, outer_its, inner_its, res_hist, (cudaStream_t)stream);
+}
+
+int ssd_ddm_sweep(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, const double *q,
+                  const double *u_prev, double *q_out, double *p_D, double *u_S, double *f_S, int inner_its[2],
+                  ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    return ddm_sweep_impl(ctx, pts, prm, q, u_prev, q_out, p_D, u_S, f_S, inner_its, (cudaStream_t)stream);
 }
 
 int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m, int *m_out,

@@ -93,6 +93,16 @@ def test_solves_fields_and_gradients_pass_their_arrays(fake):
     name, a = rec.calls[-1]
     assert name == "ssd_stokes_solve" and a[4].value == _p(f) and list(a[5]) == [0.0, 0.0, 1.0]
     assert a[6].value == _p(u)
+    prm = ssd.ddm_params(kappa=1e-2, gamma=1.0)
+    o = ssd.ddm_sweep(ctx, pts, prm, q, f)
+    name, a = rec.calls[-1]
+    assert name == "ssd_ddm_sweep" and a[3].value == _p(q) and a[4].value == _p(f)
+    assert a[5].value == _p(o["q"]) and a[6].value == _p(o["p"]) and a[7].value == _p(o["u"])
+    assert a[8].value == _p(o["f"]) and o["u"].shape == (3, n)
+    o = ssd.ddm_sweep(ctx, pts, prm, q)
+    assert rec.calls[-1][1][4] is None
+    with pytest.raises(ValueError):
+        ssd.ddm_sweep(ctx, pts, prm, q, q)
     tg = torch.randn((3, 4), dtype=torch.float64)
     out = ssd.darcy_pressure_field(ctx, pts, 1.0, 0.5, q, q, tg)
     name, a = rec.calls[-1]
