@@ -358,11 +358,37 @@ MOLECULE_CENTERS = (
 )
 
 
+# Taylor coefficients 1/j! of e^r, j = 0..13, each rounded to double
+_EXP_TAYLOR = (1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333,
+               0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05, 2.7557319223985893e-06,
+               2.755731922398589e-07, 2.505210838544172e-08, 2.08767569878681e-09, 1.6059043836821613e-10)
+_LN2_HEAD = 0.6931471803691238       # ln 2 to 32 significant bits: k * head is exact for |k| < 2^21
+_LN2_TAIL = 1.9082149292705877e-10   # ln 2 - head, rounded
+_INV_LN2 = 1.4426950408889634
+
+
+def gauss_exp(x):
+    """e^x (x <= 0) for the molecule's Gaussians by one stated method, so the
+    point set does not depend on a math library's last bits: Cody and
+    Waite's additive reduction x = k ln2 + r with k = floor(x/ln2 + 1/2) and
+    ln2 split into a head and a tail, the degree-13 Taylor polynomial of e^r
+    (|r| <= ln2/2, truncation below 5e-18) by Horner's rule, then 2^k.  Every
+    operation is one rounded IEEE operation; zero below x = -700."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.floor(x * _INV_LN2 + 0.5)
+    r = (x - k * _LN2_HEAD) - k * _LN2_TAIL
+    p = np.full_like(x, _EXP_TAYLOR[13])
+    for cj in _EXP_TAYLOR[12::-1]:
+        p = p * r + cj
+    out = np.ldexp(p, np.where(x < -700.0, 0, k).astype(np.int64))
+    return np.where(x < -700.0, 0.0, out)
+
+
 def molecule_phi(centers, r, c, X):
     s = 0.0 * X[0]
     for xk in centers:
         d2 = ((X[0] - xk[0]) ** 2 + (X[1] - xk[1]) ** 2) + (X[2] - xk[2]) ** 2
-        s = s + np.exp(-d2 / (r * r))
+        s = s + gauss_exp(-d2 / (r * r))
     return c - s
 
 
@@ -370,7 +396,7 @@ def molecule_normal(centers, r, c, X):
     g = [0.0 * X[0], 0.0 * X[0], 0.0 * X[0]]
     for xk in centers:
         d = [X[k] - xk[k] for k in range(3)]
-        e = np.exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (r * r))
+        e = gauss_exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (r * r))
         for k in range(3):
             g[k] = g[k] + e * (2.0 * d[k] / (r * r))
     gn = np.sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2])

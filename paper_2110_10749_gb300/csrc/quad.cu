@@ -282,15 +282,36 @@ __device__ int eval_line_star(const QuadGeo &g, int ax, int64_t ja, int64_t jb, 
 }
 
 // ----------------------------------------------------------------- molecule
-// phi = c - sum_k exp(-|x - x_k|^2 / r^2) (phi > 0 outside), grad phi =
-// sum_k exp(-|x - x_k|^2 / r^2) 2 (x - x_k) / r^2; the same sampling and
-// bisection as the star surfaces.
+// e^x for the Gaussians of the level set (x <= 0), by one stated method so
+// that the point set does not depend on a math library's last bits: Cody and
+// Waite's additive reduction x = k ln2 + r (k = floor(x/ln2 + 1/2), ln2 split
+// into a 32-bit head, exact when multiplied by k, and its tail), the
+// degree-13 Taylor polynomial of e^r (|r| <= ln2/2, truncation < 5e-18) by
+// Horner's rule with the coefficients 1/j! rounded to double, then scaling by
+// 2^k.  Each operation is rounded once (this file compiles without FMA
+// contraction).  Zero below x = -700.
+__device__ double gauss_exp(double x) {
+    if (x < -700.0) return 0.0;
+    const double k = floor(x * 1.4426950408889634 + 0.5);
+    const double r = (x - k * 0.6931471803691238) - k * 1.9082149292705877e-10;
+    const double c[14] = {1.0, 1.0, 0.5, 0.16666666666666666, 0.041666666666666664, 0.008333333333333333,
+                          0.001388888888888889, 0.0001984126984126984, 2.48015873015873e-05,
+                          2.7557319223985893e-06, 2.755731922398589e-07, 2.505210838544172e-08,
+                          2.08767569878681e-09, 1.6059043836821613e-10};
+    double p = c[13];
+    for (int j = 12; j >= 0; --j) p = p * r + c[j];
+    return ldexp(p, (int)k);
+}
+
+// phi = c - sum_k e^{-|x - x_k|^2 / r^2} (phi > 0 outside), grad phi =
+// sum_k e^{-|x - x_k|^2 / r^2} 2 (x - x_k) / r^2 (e^x by gauss_exp); the same
+// sampling and bisection as the star surfaces.
 __device__ double mol_phi(const QuadGeo &g, const double X[3]) {
     double s = 0.0;
     for (int k = 0; k < 4; ++k) {
         const double d0 = X[0] - g.mol[k][0], d1 = X[1] - g.mol[k][1], d2 = X[2] - g.mol[k][2];
         const double r2 = (d0 * d0 + d1 * d1) + d2 * d2;
-        s = s + exp(-r2 / (g.mr * g.mr));
+        s = s + gauss_exp(-r2 / (g.mr * g.mr));
     }
     return g.mc - s;
 }
@@ -299,7 +320,7 @@ __device__ void mol_normal(const QuadGeo &g, const double X[3], double nv[3]) {
     double G[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < 4; ++k) {
         const double d[3] = {X[0] - g.mol[k][0], X[1] - g.mol[k][1], X[2] - g.mol[k][2]};
-        const double e = exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (g.mr * g.mr));
+        const double e = gauss_exp(-((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) / (g.mr * g.mr));
         for (int q = 0; q < 3; ++q) G[q] = G[q] + e * (2.0 * d[q] / (g.mr * g.mr));
     }
     const double gn = sqrt((G[0] * G[0] + G[1] * G[1]) + G[2] * G[2]);

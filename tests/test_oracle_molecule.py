@@ -56,3 +56,17 @@ def test_volume_and_area_convergence():
     assert abs(vol[48] / vcount - 1) < 2e-4, (vol, vcount)
     assert abs(vol[32] - vol[48]) < abs(vol[16] - vol[32]) / 5
     assert abs(area[32] - area[48]) < abs(area[16] - area[32]) / 5
+
+
+def test_gauss_exp_is_exp_to_two_ulps():
+    """The molecule's stated exponential (Cody-Waite reduction, degree-13
+    Taylor polynomial) against 40-digit exp, and its exact points."""
+    mpmath = __import__("pytest").importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([-np.linspace(0.0, 60.0, 3001), -rng.uniform(0.0, 700.0, 2000), [-1e-300, -5e-17]])
+    g = Q.gauss_exp(xs)
+    worst = max(abs(float((mpmath.mpf(v) - mpmath.exp(x)) / mpmath.exp(x))) for x, v in zip(xs, g))
+    assert worst < 2.0 * 2.0 ** -53
+    assert Q.gauss_exp(np.array([0.0]))[0] == 1.0
+    assert Q.gauss_exp(np.array([-800.0]))[0] == 0.0
