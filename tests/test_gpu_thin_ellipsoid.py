@@ -1,0 +1,65 @@
+"""The thin porous ellipsoid (1, 0.6, 0.4) of Section 7.4 on the device:
+the D-N solve at h = 1/16 against the oracle's, and the self-convergence
+errors ||p_h - p_{h/2}||, ||u_h - u_{h/2}|| of the device's solves for
+h = 1/16 ... 1/128 (N = 1742 ... 110250; FP64, the finest in FP32C) against Table 3 for
+kappa = 1, 1e-2 and 1e-7 (BJS traction with gamma = 0, U = e_z,
+theta = kappa/2, tolerance 1e-9)."""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import quadrature as Q
+from oracle import solvers as S
+from test_oracle_thin_ellipsoid import coarse_in_fine
+
+pytestmark = pytest.mark.gpu
+ABC = (1.0, 0.6, 0.4)
+
+
+def _prm(ssd, h, kappa, prec):
+    # FP32C runs to the tolerances its pair-sum rounding allows
+    tol_o, tol_i = (1e-9, 1e-10) if prec == ssd.FP64 else (1e-8, 1e-9)
+    inner = ssd.krylov(tol_i, 256, 256, False, prec, deflate=prec == ssd.FP32C)
+    return ssd.ddm_params(mu=1.0, kappa=kappa, gamma=0.0, uinf=(0.0, 0.0, 1.0), delta=3 * h,
+                          theta=0.5 * min(kappa, 1.0), tol_outer=tol_o, maxit_outer=200, outer_gmres=True,
+                          traction_mode=ssd.TRACTION_BJS, bjs_sign=1.0, inner=inner)
+
+
+def test_thin_ellipsoid_solve_matches_oracle(gpu_ctx):
+    import paper_2110_10749_gb300 as ssd
+    h = 1 / 16
+    p = Q.ellipsoid_points(ABC, h)
+    P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
+    ro = S.ddm_solve(p, 3 * h, 1.0, 1.0, 0.0, [0.0, 0.0, 1.0], 0.5, tol=1e-9, maxit=60, outer="gmres",
+                     traction="bjs", inner_tol=1e-10)
+    r = ssd.ddm_solve(gpu_ctx, P, _prm(ssd, h, 1.0, ssd.FP64))
+    assert r["outer_its"] == ro["outer_its"]
+    for k in ("q", "p", "u", "f"):
+        a, b = r[k].cpu().numpy(), ro[k]
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-8, k
+    P.release()
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e-2, 1e-7])
+def test_self_convergence_matches_table3(gpu_ctx, kappa):
+    import paper_2110_10749_gb300 as ssd
+    rows = [r for r in read_golden("thin_ellipsoid_table3.txt") if float(r[0]) == kappa]
+    sols = {}
+    for hinv in (16, 32, 64, 128):
+        h = 1.0 / hinv
+        g = ssd.quadrature_points(gpu_ctx, ssd.ELLIPSOID, ABC, h)
+        P = ssd.Points(g["xyz"], g["nrm"], g["w"]).prepare(gpu_ctx)
+        # FP64 up to h = 1/64; the h = 1/128 reference (N = 110250) in FP32C
+        r = ssd.ddm_solve(gpu_ctx, P, _prm(ssd, h, kappa, ssd.FP64 if hinv <= 64 else ssd.FP32C))
+        assert r["status"] == 0
+        sols[hinv] = ({"meta": g["meta"].cpu().numpy()}, r["p"].cpu().numpy(), r["u"].cpu().numpy())
+        P.release()
+    for row in rows:
+        hinv = int(row[1])
+        (pc, pcv, ucv), (pf, pfv, ufv) = sols[hinv], sols[2 * hinv]
+        idx = coarse_in_fine(pc, pf)
+        assert (idx >= 0).all()
+        ep, eu = S.rms(pcv - pfv[idx]), S.rms(ucv - ufv[:, idx])
+        # the printed values to within 2% (their last digit and the GMRES stopping point)
+        assert abs(ep - float(row[7])) < 2e-2 * float(row[7]), (kappa, hinv, ep, row[7])
+        assert abs(eu - float(row[8])) < 2e-2 * float(row[8]), (kappa, hinv, eu, row[8])
