@@ -211,13 +211,34 @@ int ssd_stokes_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const doubl
  * points are used in caller order).  Scratch: one file-scope device array of
  * 16 MiB, held on every device that loads the library until the process
  * exits.  Limit: n rounded up to a multiple of 512 must not exceed 32768
- * (larger sets give SSD_EINVAL before any work).  The first call on a device
- * looks up the array's device address with that device current; make it
- * before any stream capture.  All calls share the array: calls whose work can
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Asynchronous on `stream`. */
+ * (larger sets give SSD_EINVAL before any work).  The context's device must
+ * be the current device (SSD_EINVAL otherwise).  The first call with a given
+ * ssd_ctx looks up the array's device address and keeps it in the ssd_ctx;
+ * make that call before any stream capture.  Like all of an ssd_ctx's device
+ * state, the address belongs to the CUDA context current when it was taken:
+ * use the ssd_ctx under that CUDA context only, and destroy it before a
+ * cudaDeviceReset.  All calls share the array: calls whose work can overlap
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Asynchronous on `stream`. */
 int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double delta, const double *u,
                           double *out, ssd_stream stream);
+/* Row blocks of the four operators, for splitting one application over
+ * several devices (each holds the whole point set and density and computes
+ * its own rows; one gather of the results per application).  Rows are
+ * positions in the point set's spatial order (the layout order that
+ * ssd_points_prepare builds, or an equal temporary one): row k is caller
+ * point order[k] of ssd_points_order.  Computes out[c][order[k]] for
+ * row_begin <= k < row_end only (the other entries of out are not written),
+ * bit-identical to the same entries of the whole application.  op: 0 = L
+ * (ssd_laplace_SL), 1 = D^L (ssd_laplace_DL), 2 = M (ssd_stokes_SL, mu
+ * used), 3 = D^S (ssd_stokes_DL); dens, out as for that call.  SSD_EINVAL
+ * unless 0 <= row_begin < row_end <= n.  Asynchronous on `stream`. */
+int ssd_apply_rows(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu,
+                   const double *dens, int64_t row_begin, int64_t row_end, double *out,
+                   int prec, ssd_stream stream);
+/* The spatial order of a point set: order[k] (host, [n]) = caller index of
+ * row k.  Synchronises `stream`. */
+int ssd_points_order(ssd_ctx *ctx, const ssd_points *pts, int32_t *order, ssd_stream stream);
 /* One pass sharing r, erf and exp between both layers:
  * out = alpha (M f) + beta (D^S u)   [Stokes],   out = alpha (L g) + beta (D^L p)   [Laplace].
  * Used for the right-hand sides and residuals b - A x of the local solves. */

@@ -35,7 +35,7 @@ EXPORTS = [
     "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count",
     "ssd_quadrature_points", "ssd_quadrature_jacobian", "ssd_points_prepare", "ssd_points_release",
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
-    "ssd_stokes_SLDL", "ssd_laplace_SLDL",
+    "ssd_stokes_SLDL", "ssd_laplace_SLDL", "ssd_apply_rows", "ssd_points_order",
     "ssd_darcy_solve", "ssd_stokes_solve", "ssd_ddm_solve", "ssd_ddm_solve_host", "ssd_ddm_sweep",
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
@@ -130,6 +130,8 @@ def lib():
         "ssd_laplace_DL": [P, C.POINTER(CPoints), d, P, P, i, P],
         "ssd_stokes_SL": [P, C.POINTER(CPoints), d, d, P, P, i, P],
         "ssd_stokes_DL": [P, C.POINTER(CPoints), d, P, P, i, P],
+        "ssd_apply_rows": [P, C.POINTER(CPoints), i, d, d, P, i64, i64, P, i, P],
+        "ssd_points_order": [P, C.POINTER(CPoints), P, P],
         "ssd_stokes_SLDL": [P, C.POINTER(CPoints), d, d, P, P, d, d, P, i, P],
         "ssd_laplace_SLDL": [P, C.POINTER(CPoints), d, P, P, d, d, P, i, P],
         "ssd_darcy_solve": [P, C.POINTER(CPoints), d, d, d, P, P, C.POINTER(CKrylov), C.POINTER(i),
@@ -376,6 +378,27 @@ def stokes_DL(ctx, pts, delta, u, prec=FP64, out=None):
     ctx.check(lib().ssd_stokes_DL(ctx.h, C.byref(pts.c), float(delta), _arg(u, n3, dv, "u"),
                                   _arg(out, n3, dv, "out"), prec, _stream()), "ssd_stokes_DL")
     return out
+
+
+def apply_rows(ctx, pts, op, delta, dens, row_begin, row_end, mu=1.0, prec=FP64, out=None):
+    """Rows [row_begin, row_end) of the spatial order of op (OP_LAPLACE_SL/DL,
+    OP_STOKES_SL/DL) applied to dens; only those rows of `out` are written
+    (a new zero-filled array when out is None)."""
+    if out is None:
+        out = _torch().zeros_like(dens)
+    m, dv = _nc(op) * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_apply_rows(ctx.h, C.byref(pts.c), int(op), float(delta), float(mu), _arg(dens, m, dv, "dens"),
+                                   int(row_begin), int(row_end), _arg(out, m, dv, "out"), int(prec), _stream()),
+              "ssd_apply_rows")
+    return out
+
+
+def points_order(ctx, pts):
+    """Spatial order of the point set: numpy int32 [n], caller index of each row."""
+    order = np.empty(pts.n, dtype=np.int32)
+    ctx.check(lib().ssd_points_order(ctx.h, C.byref(pts.c), order.ctypes.data_as(C.c_void_p), _stream()),
+              "ssd_points_order")
+    return order
 
 
 def apply_transpose(ctx, pts, op, delta, dens, mu=1.0, prec=FP64, out=None):

@@ -78,6 +78,7 @@ struct ssd_ctx {
     int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
     int lpt = 1;               // pair grids in near-first order on prepared layouts
     int waves64 = 8;           // FP64 grid: about this many waves of resident CTAs (tuned)
+    void *noalloc_scratch = nullptr;   // device address of the no-alloc scratch array (first no-alloc call)
     std::string err;
     // caching device allocator: blocks are reused in stream order
     struct Block { void *p; size_t bytes; bool used; };
@@ -152,6 +153,7 @@ struct PairCall {
     const double *rank1_nrm = nullptr;    // vector ops: add n (w . (dens0 . n)) / sum(w) (Stokes
                                           // normal-mode deflation); caller-order normals [3][n]
     bool transpose_sl = false;            // OP_LSL / OP_SSL: apply the transpose W S W^{-1}
+    int64_t row_begin = 0, row_end = -1;  // layout rows [row_begin, row_end) only (row_end < 0: all rows)
     double *out = nullptr;
 };
 int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s);

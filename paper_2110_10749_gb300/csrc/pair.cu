@@ -20,7 +20,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
 
 #include "internal.h"
 #include "erfcx_coef.h"
@@ -102,6 +101,7 @@ template <typename R> struct KArgs {
     int64_t rec_stride;        // density records per right-hand side
     int64_t part_stride;       // partial values per right-hand side
     const int2 *order = nullptr;   // single-surface launch order: blockIdx.x -> (target tile, split)
+    int64_t tile0 = 0;             // single-surface launch without order: first target tile
 };
 
 // Smoothed radial factors k1 = s1/r, k2 = s2/r^3, k3 = s3/r^3, k4 = s4/r^5
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
         part_base = blockIdx.y * a.part_stride + NC * NSL * sf.pbase + (int64_t)it.split * NC * NSL * sf.n_pad - sf.poff;
         pstride = sf.n_pad;
     } else {
-        int64_t bt = blockIdx.x, bs = blockIdx.y;
+        int64_t bt = blockIdx.x + a.tile0, bs = blockIdx.y;
         if (a.order) {
             const int2 o = a.order[blockIdx.x];
             bt = o.x;
@@ -370,6 +370,7 @@ struct K32Args {
     // split)), and 1 partial slot per target when every CTA holds one tile
     const int2 *order = nullptr;
     int nslot = 2;
+    int64_t tile0 = 0;          // single-surface launch without order: first target tile
 };
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
         part_base = blockIdx.y * a.part_stride + NC * 2 * sf.pbase + (int64_t)it.split * NC * 2 * sf.n_pad - sf.poff;
         pstride = sf.n_pad;
     } else {
-        int64_t bt = blockIdx.x, bs = blockIdx.y;
+        int64_t bt = blockIdx.x + a.tile0, bs = blockIdx.y;
         if (a.order) {
             const int2 o = a.order[blockIdx.x];
             bt = o.x;
@@ -741,6 +742,7 @@ struct EpiArgs {
     double wdot_scale;
     const double *rank1_nrm; // caller order [3][n]
     double *out;
+    int64_t row0 = 0, row1 = -1;   // only layout rows [row0, row1) are written (row1 < 0: all)
 };
 
 __global__ void epilogue_kernel(const EpiArgs a) {
@@ -764,6 +766,7 @@ __global__ void epilogue_kernel(const EpiArgs a) {
     if (g >= a.n_pad * a.nc) return;
     const int q = (int)(g / a.n_pad);
     const int64_t i = g - (int64_t)q * a.n_pad;
+    if (a.row1 >= 0 && (i < a.row0 || i >= a.row1)) return;
     const int32_t o = a.perm[i];
     if (o < 0) return;
     // four interleaved partial sums over the splits (loads stay in flight),
@@ -1187,9 +1190,17 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     SSD_TRY(launch_check(ctx, "pack kernel"));
 
     const int cls = kernel_class(op);
+    // a row block (layout rows [row_begin, row_end)) launches only the target
+    // tiles that cover it, with the splits of the whole operator, so every
+    // row's sum is the one the whole operator computes
+    const bool rows = pc.row_end >= 0;
+    const int64_t tile0 = rows ? pc.row_begin / tspan : 0;
+    const int64_t tile1 = rows ? (pc.row_end + tspan - 1) / tspan : ntiles_t;
+    if (rows && !(pc.row_begin >= 0 && pc.row_begin < pc.row_end && pc.row_end <= n))
+        return set_error(ctx, SSD_EINVAL, "row block must satisfy 0 <= row_begin < row_end <= n");
     cudaEvent_t ev = nullptr;
     SSD_TRY(timed_begin(ctx, s, &ev));
-    dim3 grid((unsigned)ntiles_t, (unsigned)nsplit);
+    dim3 grid((unsigned)(tile1 - tile0), (unsigned)nsplit);
     cudaError_t e;
     if (f32 && transposed) {
         KArgs<float> ka;
@@ -1200,6 +1211,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.c = make_consts<float>(pc.delta, kRhoFar32);
         ka.part = reinterpret_cast<float *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+        ka.tile0 = tile0;
         e = launch_transpose<float>(op, grid, ka, s);
     } else if (f32) {
         K32Args ka;
@@ -1211,8 +1223,9 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.part = reinterpret_cast<float *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
         ka.nslot = nslot;
+        ka.tile0 = tile0;
         dim3 g = grid;
-        if (ctx->lpt && L.order_ok) {
+        if (ctx->lpt && L.order_ok && !rows) {
             const int2 *ord = nullptr;
             const int st = item_order(ctx, L, 0, kTPB32, kTPT32, ntiles_t, nsplit, chunk, ka.c.rfar2, &ord, s);
             if (st != SSD_OK) return st;
@@ -1229,8 +1242,9 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
         ka.c = make_consts<double>(pc.delta, kRhoFar64);
         ka.part = reinterpret_cast<double *>(base + o_part);
         ka.items = nullptr; ka.surfs = nullptr; ka.consts = nullptr; ka.rec_stride = 0; ka.part_stride = 0;
+        ka.tile0 = tile0;
         dim3 g = grid;
-        if (ctx->lpt && L.order_ok) {
+        if (ctx->lpt && L.order_ok && !rows) {
             const int2 *ord = nullptr;
             const int st = item_order(ctx, L, 1, kTPB64, kTPT64, ntiles_t, nsplit, chunk,
                                       (float)ka.c.rfar2, &ord, s);
@@ -1242,7 +1256,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     }
     ctx->launches++;
     if (e != cudaSuccess) return cuda_check(ctx, e, "pair kernel launch");
-    timed_end(ctx, s, ev, cls, pc.prec, (double)n * (double)n);
+    timed_end(ctx, s, ev, cls, pc.prec, (double)(rows ? pc.row_end - pc.row_begin : n) * (double)n);
 
     EpiArgs ea{};
     ea.perm = L.perm; ea.n = n; ea.n_pad = n_pad; ea.nc = nc; ea.nsplit = (int)nsplit; ea.nslot = nslot;
@@ -1255,6 +1269,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     ea.rank1_nrm = pc.rank1_nrm;
     ea.weight_out = tsl ? 1 : 0;
     ea.out = pc.out;
+    if (rows) { ea.row0 = pc.row_begin; ea.row1 = pc.row_end; }
     epilogue_kernel<<<(unsigned)((n_pad * nc + 127) / 128), 128, 0, s>>>(ea);
     ctx->launches++;
     return launch_check(ctx, "epilogue kernel");
@@ -1527,10 +1542,6 @@ constexpr size_t kNoAllocBytes = 16u << 20;              // 16 MiB per device
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-static void *g_noalloc_ptr[kMaxDevices];
-static std::mutex g_noalloc_mu;
-
 // unsorted layout of the caller's points inside the scratch array
 __global__ void noalloc_layout_kernel(const double *xyz, const double *nrm, const double *w, int64_t n,
                                       int64_t n_pad, Layout L) {
@@ -1575,20 +1586,23 @@ __global__ void noalloc_chunk_box_kernel(Layout L) {
     L.cbox[2 * c + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
 }
 
-// Device address of the scratch array for the current device; looked up
-// once per device (host code must not pass the symbol itself to a kernel).
+// Device address of the scratch array on the context's device, looked up
+// at the context's first no-alloc call with that device current and kept in
+// the ssd_ctx (host code must not pass the symbol itself to a kernel).  The
+// address belongs to the CUDA context current at that call, like the rest of
+// the ssd_ctx's device state.
 int noalloc_scratch(ssd_ctx *ctx, char **out) {
     int dev = 0;
     SSD_TRY(cuda_check(ctx, cudaGetDevice(&dev), "cudaGetDevice"));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(ctx, SSD_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (dev != ctx->device)
+        return set_error(ctx, SSD_EINVAL, "ssd_stokes_DL_noalloc: the current device is not the context's device");
+    if (!ctx->noalloc_scratch) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_check(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_ptr[dev] = p;
+        ctx->noalloc_scratch = p;
     }
-    *out = static_cast<char *>(g_noalloc_ptr[dev]);
+    *out = static_cast<char *>(ctx->noalloc_scratch);
     return SSD_OK;
 }
 

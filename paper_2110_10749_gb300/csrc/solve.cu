@@ -1587,6 +1587,32 @@ int ssd_stokes_DL(ssd_ctx *ctx, const ssd_points *pts, double delta, const doubl
     return op_entry(ctx, pts, pc, (cudaStream_t)stream);
 }
 
+int ssd_apply_rows(ssd_ctx *ctx, const ssd_points *pts, int op, double delta, double mu, const double *dens,
+                   int64_t row_begin, int64_t row_end, double *out, int prec, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (op < OP_LSL || op > OP_SDL) return set_error(ctx, SSD_EINVAL, "op must be one of the four layer operators");
+    if (!pts || row_begin < 0 || row_end <= row_begin || row_end > pts->n)
+        return set_error(ctx, SSD_EINVAL, "row block must satisfy 0 <= row_begin < row_end <= n");
+    PairCall pc;
+    pc.op = op; pc.prec = prec; pc.delta = delta; pc.mu = mu; pc.dens0 = dens; pc.out = out;
+    pc.row_begin = row_begin; pc.row_end = row_end;
+    return op_entry(ctx, pts, pc, (cudaStream_t)stream);
+}
+
+int ssd_points_order(ssd_ctx *ctx, const ssd_points *pts, int32_t *order, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    if (!order) return set_error(ctx, SSD_EINVAL, "NULL output");
+    SSD_TRY(check_points(ctx, pts));
+    cudaStream_t s = (cudaStream_t)stream;
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(order, lref.L->perm, sizeof(int32_t) * pts->n, cudaMemcpyDeviceToHost, s),
+                       "order copy"));
+    return cuda_check(ctx, cudaStreamSynchronize(s), "order sync");
+}
+
 int ssd_stokes_SLDL(ssd_ctx *ctx, const ssd_points *pts, double delta, double mu, const double *f, const double *u,
                     double alpha, double beta, double *out, int prec, ssd_stream stream) {
     if (!ctx) return SSD_EINVAL;

@@ -69,6 +69,14 @@ def test_operators_pass_their_arrays(fake):
     name, a = rec.calls[-1]
     assert name == "ssd_stokes_SLDL" and a[4].value == _p(v2) and a[5].value == _p(v)
     assert (a[6], a[7]) == (0.5, -1.0) and a[8].value == _p(out) and out.shape == (3, n)
+    out = ssd.apply_rows(ctx, pts, ssd.OP_STOKES_DL, 0.1, v, 2, 7, mu=1.5, prec=ssd.FP32C)
+    name, a = rec.calls[-1]
+    assert name == "ssd_apply_rows" and a[2] == ssd.OP_STOKES_DL and a[4] == 1.5 and a[5].value == _p(v)
+    assert (a[6], a[7]) == (2, 7) and a[8].value == _p(out) and a[9] == ssd.FP32C and out.shape == (3, n)
+    with pytest.raises(ValueError):
+        ssd.apply_rows(ctx, pts, ssd.OP_LAPLACE_DL, 0.1, v, 0, 3)
+    order = ssd.points_order(ctx, pts)
+    assert rec.calls[-1][0] == "ssd_points_order" and order.shape == (n,) and order.dtype == np.int32
     out = ssd.apply_transpose(ctx, pts, ssd.OP_LAPLACE_DL, 0.1, g)
     assert rec.calls[-1][0] == "ssd_apply_transpose" and out.shape == (n,)
     ssd.apply_transpose(ctx, pts, ssd.OP_STOKES_DL, 0.1, v)
