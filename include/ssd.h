@@ -430,6 +430,13 @@ int ssd_hessenberg_eigenvalues(int n, const double *h /* host */, int ldh, doubl
  * Stokes velocity outside, eq. Stokes with n_S = -n and 1/(8 pi mu):
  *   u_S(y) = U_inf - 1/(8 pi mu) sum_j w_j S(y - x_j) f_j
  *            + 6/(8 pi) sum_j w_j (u_j . yh)(yh . n_j) yh / r^5;  out[3][nt].
+ * Stokes pressure outside (the paper prints the velocity representation only;
+ * these are the pressures that go with its two kernels, the Stokeslet's
+ * 2 yh / r^3 and the stresslet's 4 (-I / r^3 + 3 yh yh / r^5), far-field
+ * pressure 0):
+ *   p_S(y) = -1/(8 pi) sum_j w_j 2 (yh . f_j) / r^3
+ *            - mu/(8 pi) sum_j w_j 4 [-(u_j . n_S) / r^3 + 3 (yh . u_j)(yh . n_S) / r^5];
+ *   out[nt].
  * q, p_D, f, u are the outputs of ssd_ddm_solve.  Asynchronous on `stream`.
  */
 int ssd_darcy_pressure_field(ssd_ctx *ctx, const ssd_points *pts, double mu, double kappa,
@@ -438,6 +445,9 @@ int ssd_darcy_pressure_field(ssd_ctx *ctx, const ssd_points *pts, double mu, dou
 int ssd_stokes_velocity_field(ssd_ctx *ctx, const ssd_points *pts, double mu,
                               const double uinf[3] /* host */, const double *f, const double *u,
                               int64_t nt, const double *targets, double *out, ssd_stream stream);
+int ssd_stokes_pressure_field(ssd_ctx *ctx, const ssd_points *pts, double mu, const double *f,
+                              const double *u, int64_t nt, const double *targets, double *out,
+                              ssd_stream stream);
 
 /* ---------------------------------------------------------------- adjoint
  * Derivatives of a scalar output of the Dirichlet-Neumann solve with respect

@@ -56,3 +56,26 @@ def stokes_velocity_field(pts, f, u, mu, uinf, targets):
         out[:, a:b] = (np.asarray(uinf, dtype=np.float64)[:, None]
                        - single.sum(2) / (8.0 * math.pi * mu) + double.sum(2) / (8.0 * math.pi))
     return out
+
+
+def stokes_pressure_field(pts, f, u, mu, targets):
+    """p_S(y) = -1/(8 pi) int P . f dS - mu/(8 pi) int u . Pi . n_S dS, y
+    outside, with the pressures that go with the kernels of eq. Stokes: the
+    Stokeslet's P_i = 2 yh_i / r^3 and the stresslet's
+    Pi_ik = 4 (-delta_ik / r^3 + 3 yh_i yh_k / r^5), yh = y - x, n_S = -n;
+    the far-field pressure is 0.  The paper prints the velocity
+    representation only; this is its pressure counterpart."""
+    x, n, w = pts["xyz"], pts["nrm"], pts["w"]
+    y = np.asarray(targets, dtype=np.float64)
+    out = np.empty(y.shape[1])
+    nS = -n
+    for a, b in _chunks(y.shape[1]):
+        d = y[:, a:b, None] - x[:, None, :]            # [3][t][s]
+        r = np.sqrt((d * d).sum(0))
+        single = 2.0 * (d * f[:, None, :]).sum(0) / r ** 3 * w
+        du = (d * u[:, None, :]).sum(0)
+        dn = (d * nS[:, None, :]).sum(0)
+        un = (u * nS).sum(0)
+        double = 4.0 * (-un[None, :] / r ** 3 + 3.0 * du * dn / r ** 5) * w
+        out[a:b] = -single.sum(1) / (8.0 * math.pi) - mu * double.sum(1) / (8.0 * math.pi)
+    return out

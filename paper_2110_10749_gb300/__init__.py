@@ -40,7 +40,7 @@ EXPORTS = [
     "ssd_batch_prepare", "ssd_batch_release", "ssd_batch_apply", "ssd_batch_ddm_solve",
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
-    "ssd_darcy_pressure_field", "ssd_stokes_velocity_field", "ssd_ddm_spectrum",
+    "ssd_darcy_pressure_field", "ssd_stokes_velocity_field", "ssd_stokes_pressure_field", "ssd_ddm_spectrum",
     "ssd_hessenberg_eigenvalues",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
@@ -154,6 +154,7 @@ def lib():
         "ssd_ddm_spectrum": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i, C.POINTER(i), C.POINTER(d),
                              C.POINTER(d), C.POINTER(d), P],
         "ssd_stokes_velocity_field": [P, C.POINTER(CPoints), d, C.POINTER(d), P, P, i64, P, P, P],
+        "ssd_stokes_pressure_field": [P, C.POINTER(CPoints), d, P, P, i64, P, P, P],
         "ssd_hessenberg_eigenvalues": [i, C.POINTER(d), i, C.POINTER(d), C.POINTER(d)],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
@@ -631,6 +632,18 @@ def stokes_velocity_field(ctx, pts, mu, uinf, f, u, targets, out=None):
     ctx.check(lib().ssd_stokes_velocity_field(ctx.h, C.byref(pts.c), float(mu), ui, _arg(f, n3, dv, "f"),
                                               _arg(u, n3, dv, "u"), nt, _arg(targets, 3 * nt, dv, "targets"),
                                               _arg(out, 3 * nt, dv, "out"), _stream()), "ssd_stokes_velocity_field")
+    return out
+
+
+def stokes_pressure_field(ctx, pts, mu, f, u, targets, out=None):
+    """Stokes pressure at field points outside the body (far-field pressure 0)."""
+    torch = _torch()
+    nt = int(targets.shape[1])
+    out = out if out is not None else torch.empty((nt,), dtype=torch.float64, device=targets.device)
+    n3, dv = 3 * pts.n, pts.xyz.device
+    ctx.check(lib().ssd_stokes_pressure_field(ctx.h, C.byref(pts.c), float(mu), _arg(f, n3, dv, "f"),
+                                              _arg(u, n3, dv, "u"), nt, _arg(targets, 3 * nt, dv, "targets"),
+                                              _arg(out, nt, dv, "out"), _stream()), "ssd_stokes_pressure_field")
     return out
 
 

@@ -45,6 +45,13 @@ def test_fields_match_oracle_and_porous_sphere(gpu_ctx, kappa):
     uo = F.stokes_velocity_field(p, f, u, 1.0, [0.0, 0.0, 1.0], to)
     assert np.abs(pg - po).max() <= 1e-12 * np.abs(po).max()
     assert np.abs(ug - uo).max() <= 1e-12 * np.abs(uo).max()
+    # the Stokes pressure outside: against the oracle, and against the
+    # porous sphere's mu U A1 cos(theta) / r^2 with A1 = -3R/(2 + kappa/R^2)
+    sg = ssd.stokes_pressure_field(gpu_ctx, P, 1.0, r["f"], r["u"], T(to)).cpu().numpy()
+    so = F.stokes_pressure_field(p, f, u, 1.0, to)
+    assert np.abs(sg - so).max() <= 1e-12 * np.abs(so).max()
+    sex = -3.0 / (2.0 + kappa) * to[2] / np.sqrt((to * to).sum(0)) ** 3
+    assert np.abs(sg - sex).max() < 2e-2 * np.abs(sex).max()
     # the porous sphere in the bulk, to the discretisation error of h = 1/8
     assert np.abs(pg - A.jt_pressure_darcy(ti, 1.0, kappa, 1.0, [0.0, 0.0, 1.0])).max() < 1e-2
     assert np.abs(ug - A.jt_velocity_stokes(to, 1.0, kappa, 1.0, [0.0, 0.0, 1.0])).max() < 1e-2

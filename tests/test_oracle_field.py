@@ -2,6 +2,8 @@
 exact fields reproduced from their own Cauchy data, and the Joseph-Tao
 porous sphere (Section 7.3) reproduced in the bulk from the D-N solution,
 with errors that fall at high order as h is refined."""
+import math
+
 import numpy as np
 import pytest
 
@@ -56,3 +58,31 @@ def test_porous_sphere_bulk_fields(kappa):
         errs.append((ep, eu))
     assert errs[0][0] < 1e-2 and errs[0][1] < 1e-2, errs
     assert errs[1][0] < errs[0][0] / 6 and errs[1][1] < errs[0][1] / 6, errs
+
+
+def test_stokes_pressure_representation():
+    """The pressure counterpart of eq. Stokes reproduces two exact exterior
+    pressures from their boundary data, with an error falling with h: the
+    Stokeslet placed inside the body, and the porous sphere with slip
+    (p_S = mu U A1 cos(theta) / r^2)."""
+    errs = []
+    for h in (1 / 8, 1 / 16):
+        R, mu = 0.8, 1.3
+        p = Q.sphere_points(R, h)
+        x0, Fv = np.array([0.2, 0.0, 0.0]), np.array([1.0, 0.3, -0.5])
+        u, sig = A.stokeslet(p["xyz"], x0, Fv, mu)
+        f = np.einsum("ikn,kn->in", sig, p["nrm"])
+        t = _shell(1.6, 30, 7)
+        d = t - x0[:, None]
+        pex = (Fv @ d) / (4.0 * math.pi * np.sqrt((d * d).sum(0)) ** 3)
+        e1 = np.abs(F.stokes_pressure_field(p, f, u, mu, t) - pex).max() / np.abs(pex).max()
+        ps = Q.sphere_points(1.0, h)
+        kappa, gamma = 1e-2, 1.0
+        _, _, us, fs = A.bjs_interface_fields(ps["xyz"], 1.0, kappa, gamma, 1.0, (0.0, 0.0, 1.0))
+        x, _ = A.bjs_sphere_coefficients(1.0, kappa, gamma)
+        t2 = _shell(1.5, 30, 8)
+        pexs = x * t2[2] / np.sqrt((t2 * t2).sum(0)) ** 3
+        e2 = np.abs(F.stokes_pressure_field(ps, fs, us, 1.0, t2) - pexs).max() / np.abs(pexs).max()
+        errs.append((e1, e2))
+    assert errs[0][0] < 2e-2 and errs[0][1] < 1e-2, errs
+    assert errs[1][0] < errs[0][0] / 8 and errs[1][1] < errs[0][1] / 8, errs
