@@ -1,23 +1,35 @@
 #!/usr/bin/env python
 """Benchmark of the Stokes-Darcy Dirichlet-Neumann solve on one GB300.
 
-Workload (one step): the unit sphere at h = 1/32 (N = 17070 quadrature points,
-delta = 3h), mu = 1, U = e_z, BJS traction with gamma in {0.1, 1} and
-kappa in {1, 1e-2, 1e-4} (six D-N solves, theta = 0.5 min(kappa, 1)),
-interface GMRES to 1e-8 with local GMRES to 1e-9 (one Krylov cycle each).
-Pair sums in FP32C (FP32 terms, compensated accumulation), Krylov and
-interface arithmetic in FP64.  The plain FP64 comparison solves run to the
-paper's 1e-9 / 1e-10.
-The BJS slip is imposed implicitly in the Stokes step (one fused SL+DL pass
-per matvec).
+Headline workload: the ellipsoid with axes (1, 0.7, 0.5) at h = 1/128
+(N = 138830 quadrature points, 1.93e10 pairs per operator application),
+delta = 3h, mu = 1, U = e_z, kappa = 1e-3, BJS slip gamma = 1 lagged one
+sweep (Section 3, step 2), theta = kappa/2, interface GMRES to 1e-8, local
+GMRES to 1e-9 (one Krylov cycle each).  Pair sums in FP32C (FP32 terms,
+compensated accumulation); Krylov, interface and epilogue arithmetic in FP64.
 
-Metric: pair-interactions/s, i.e. ordered (target, source) pairs evaluated
-by the pair kernels over the whole step divided by the step's device time.
-Beside it: time-to-solution of each solve in FP32C and in plain FP64 (both
-on the GPU) and the FP32C-vs-FP64 difference of every output.
+One step is one D-N sweep (Section 6, steps (a)-(f): Laplace single layer,
+Darcy GMRES on the Laplace double layer, traction, Stokes single layer,
+Stokes GMRES on the Stokes double layer, q update) from the converged
+interface state, i.e. the unit of work the interface GMRES repeats until it
+converges.  Metric: pair-interactions/s, the ordered (target, source) pairs
+the pair kernels evaluate over the timed sweeps divided by their device
+time.  Beside it: the time-to-solution of the whole D-N solve (FP32C), the
+fixed-point residual of its solution under one plain-FP64 sweep, the FP64
+sweep time, and the end-to-end solve through the host-buffer C entry point.
+
+Second section: the unit sphere at h = 1/32 (N = 17070), kappa in
+{1, 1e-2, 1e-4} x gamma in {0.1, 1}: time-to-solution of each solve in FP32C
+and in plain FP64 (both on the GPU, same tolerances) and their difference.
+
+The oracle leg (rank 0, --skip-cpu to leave out) times the FP64 CPU oracle
+on the host cores and checks the device's results with it: the errors of the
+sphere solves against the porous sphere with slip (the oracle's closed
+form), and the residual of the ellipsoid solution in the oracle's operators
+on sampled target rows.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+on a bounded sample of the headline workload instead.
 """
 from __future__ import annotations
 
@@ -25,6 +37,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -36,41 +49,54 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-H = 1.0 / 32
+# headline: ellipsoid (1, 0.7, 0.5), h = 1/128
+ABC5 = (1.0, 0.7, 0.5)
+H5 = 1.0 / 128
+KAPPA5, GAMMA5 = 1e-3, 1.0
+# second section: unit sphere, h = 1/32
+H2 = 1.0 / 32
 KAPPAS = (1.0, 1e-2, 1e-4)
 ALPHAS = (0.1, 1.0)
-# FP32C runs to tolerances its arithmetic can reach (pair sums carry ~1e-7
-# relative rounding); the plain FP64 comparison runs to the paper's 1e-9/1e-10.
-TOL = {"fp32c": (1e-8, 1e-9), "fp64": (1e-9, 1e-10)}
+TOL_OUTER, TOL_INNER = 1e-8, 1e-9
 METRIC = "pair-interactions/s (SL+DL matvec) & DDM time-to-solution at stated error, FP32c vs FP64"
 UNIT = "pair-interactions/s"
-# Nominal FP32 flops per pair of the Stokes double layer (FMA = 2, rsqrt,
-# exp and erf counted as one each): far pairs (s4 = 1) and near pairs
-# (rho < 5.5, smoothed kernel).
-FLOPS_SDL_FAR = 33
-FLOPS_SDL_NEAR = 50
 RHO_FAR = 5.5
-DRAM_BYTES_SSLDL = 1201152
+# Nominal FP32 flops per ordered pair (FMA = 2, every special-function
+# operation - rsqrt, exp, erf - counted as one), fixed from the written
+# formulas: (far pair with s_i = 1, near pair rho < 5.5 with the smoothed
+# kernel).  Indexed by kernel class (Laplace SL, Laplace DL, Stokes SL,
+# Stokes DL, fused Stokes SL+DL, fused Laplace SL+DL).  A pair is one ordered
+# (target, source) evaluation, counted the same way when both directions of a
+# pair are evaluated together.
+FLOPS = {0: (11, 23), 1: (17, 29), 2: (26, 54), 3: (31, 50), 4: (51, 83), 5: (19, 38)}
+KNAMES = ["laplace_SL", "laplace_DL", "stokes_SL", "stokes_DL", "stokes_SLDL", "laplace_SLDL"]
+# DRAM bytes (read + write) per launch of the dominant kernel on the headline
+# workload, from one ncu capture, keyed by kernel class; None when no capture
+# of the current kernel exists
+DRAM_BYTES = {}
 L2_FLUSH_BYTES = 256 << 20
 
 
 def workload_config():
-    return {"workload": "unit sphere h=1/32 (N=17070), delta=3h, BJS traction, kappa in {1,1e-2,1e-4} x "
-                        "alpha in {0.1,1}, D-N by interface GMRES; FP32C to 1e-8 (local GMRES 1e-9), "
-                        "FP64 comparison to 1e-9 (local 1e-10)",
-            "n_points": 17070, "solves_per_step": 6, "pair_sums": "FP32C (compensated)",
-            "krylov": "FP64", "bjs": "implicit", "l2": "flushed before every timed step (inputs 1.4 MB < L2)"}
+    return {"workload": "ellipsoid (1,0.7,0.5) h=1/128 (N=138830), delta=3h, kappa=1e-3, BJS gamma=1 lagged "
+                        "(Section 3 step 2), theta=kappa/2, D-N by interface GMRES to 1e-8 (local GMRES 1e-9); "
+                        "step = one D-N sweep from the converged state",
+            "n_points": 138830, "pairs_per_operator": 138830 ** 2, "pair_sums": "FP32C (compensated)",
+            "krylov": "FP64", "bjs": "lagged", "second_section": "unit sphere h=1/32 (N=17070), kappa in "
+            "{1,1e-2,1e-4} x gamma in {0.1,1}, FP32C vs FP64 solves",
+            "l2": "flushed before every timed step; the operator inputs (5.5 MB of sources) stay L2-resident "
+                  "within a step by design"}
 
 
-def ddm_prm(ssd, kappa, alpha, prec, maxit_outer=200):
+def ddm_prm(ssd, h, kappa, alpha, prec, maxit_outer=512):
     # one Krylov cycle per local solve (restart = maxit): in FP32C a restart
-    # recomputes the true residual, which sits at the pair-sum rounding level
-    tol_outer, tol_inner = TOL["fp32c" if prec == ssd.FP32C else "fp64"]
-    inner = ssd.krylov(tol_inner, 256, 256, False, prec, deflate=True)
-    return ssd.ddm_params(mu=1.0, kappa=kappa, gamma=alpha, uinf=(0.0, 0.0, 1.0), delta=3 * H,
-                          theta=0.5 * min(kappa, 1.0), tol_outer=tol_outer, maxit_outer=maxit_outer,
+    # recomputes the true residual, which sits at the pair-sum rounding level;
+    # the Stokes normal mode is deflated in both precisions
+    inner = ssd.krylov(TOL_INNER, 256, 256, False, prec, deflate=True)
+    return ssd.ddm_params(mu=1.0, kappa=kappa, gamma=alpha, uinf=(0.0, 0.0, 1.0), delta=3 * h,
+                          theta=0.5 * min(kappa, 1.0), tol_outer=TOL_OUTER, maxit_outer=maxit_outer,
                           outer_gmres=True, traction_mode=ssd.TRACTION_BJS, bjs_sign=1.0, inner=inner,
-                          bjs_implicit=True)
+                          bjs_implicit=False)
 
 
 class ClockSampler:
@@ -129,18 +155,29 @@ def near_fraction(xyz, delta, rng_seed=7, sample=1024):
     return float((d2 < (RHO_FAR * delta) ** 2).mean())
 
 
-def oracle_pair_rate(budget_s, xyz, nrm, w, delta):
-    """FP64 oracle pair rate (pairs/s) on sampled target rows of the two
-    double layers (the dominant operators), repeated for about budget_s."""
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k = line.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ------------------------------------------------------------- oracle leg
+def oracle_sample_rate(budget_s, pts, delta, stride=64):
+    """FP64 oracle pairs/s of the two double layers (the matvecs of the local
+    solves) on every stride-th target row, repeated for about budget_s."""
     import oracle
-    pts = {"xyz": xyz, "nrm": nrm, "w": w}
-    n = w.size
-    rows = np.arange(0, n, 64)
+    n = pts["w"].size
+    rows = np.arange(0, n, stride)
     rng = np.random.default_rng(12345)
     u = rng.normal(size=(3, n))
     p = rng.normal(size=n)
-    pairs, t0 = 0.0, time.perf_counter()
-    calls = 0
+    pairs, calls, t0 = 0.0, 0, time.perf_counter()
     while True:
         oracle.stokes_dl(pts, delta, u, rows=rows)
         oracle.laplace_dl(pts, delta, p, rows=rows)
@@ -149,21 +186,108 @@ def oracle_pair_rate(budget_s, xyz, nrm, w, delta):
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return pairs / el, {"cores": oracle.num_threads(),
-                        "sample": "%d x (Stokes DL + Laplace DL) on every 64th target row (%d rows x %d sources)"
-                                  % (calls, rows.size, n)}
+    return pairs / el, "%d x (Stokes DL + Laplace DL) on every %dth target row (%d rows x %d sources)" % (
+        calls, stride, rows.size, n)
 
 
-def oracle_single_thread_rate(budget_s, xyz, nrm, w, delta):
-    """The same sampled oracle work on one OpenMP thread (thread count restored after)."""
+def oracle_operator_rates(pts, delta, stride=1):
+    """Pairs/s of each of the four operators (full, or every stride-th target
+    row scaled to the full operator)."""
     import oracle
+    n = pts["w"].size
+    rng = np.random.default_rng(1)
+    g, v = rng.normal(size=n), rng.normal(size=(3, n))
+    rows = np.arange(0, n, stride)
+    tg = pts["xyz"][:, rows]
+    out = {}
+    for name, fn in (("laplace_SL", lambda: oracle.laplace_sl(pts, delta, g, targets=tg)),
+                     ("laplace_DL", lambda: oracle.laplace_dl(pts, delta, g, rows=rows)),
+                     ("stokes_SL", lambda: oracle.stokes_sl(pts, delta, 1.0, v, targets=tg)),
+                     ("stokes_DL", lambda: oracle.stokes_dl(pts, delta, v, rows=rows))):
+        t0 = time.perf_counter()
+        fn()
+        out[name] = rows.size * n / (time.perf_counter() - t0)
+    return out
+
+
+def oracle_leg(args, c5, c2rows, xyz5, nrm5, w5, xyz2, nrm2, w2):
+    """Oracle timings on the host cores and the oracle's checks of the
+    device's results (the one part of the GPU run that executes oracle/)."""
+    import oracle
+    from oracle import analytic as A
+    from oracle import quadrature as Q
+    from oracle import solvers as S
+    oracle.build()
+    pts5 = {"xyz": xyz5, "nrm": nrm5, "w": w5}
+    pts2 = {"xyz": xyz2, "nrm": nrm2, "w": w2}
+    rate, sample = oracle_sample_rate(args.cpu_seconds, pts5, 3 * H5)
     cores = oracle.num_threads()
     oracle.set_num_threads(1)
     try:
-        rate, info = oracle_pair_rate(budget_s, xyz, nrm, w, delta)
+        rate1, _ = oracle_sample_rate(0.1 * args.cpu_seconds, pts5, 3 * H5)
     finally:
         oracle.set_num_threads(cores)
-    return {"value": rate, "cores": info["cores"], "sample": info["sample"]}
+    pts1 = Q.sphere_points(1.0, 1.0 / 8)
+    t0 = time.perf_counter()
+    r1 = S.ddm_solve(pts1, 3.0 / 8, 1.0, 1.0, 0.0, (0.0, 0.0, 1.0), 0.75, tol=1e-9, maxit=60, outer="gmres",
+                     traction="jt")
+    c1_s = time.perf_counter() - t0
+    rates = {"sphere h=1/8 (N=%d), full" % pts1["w"].size: oracle_operator_rates(pts1, 3.0 / 8),
+             "sphere h=1/32 (N=%d), full" % w2.size: oracle_operator_rates(pts2, 3 * H2),
+             "ellipsoid h=1/128 (N=%d), every 64th target row, scaled" % w5.size:
+                 oracle_operator_rates(pts5, 3 * H5, stride=64)}
+    # C2 time-to-solution of the oracle, extrapolated: its measured
+    # per-operator time at N = 17070 times the device solve's operator counts
+    r2 = rates["sphere h=1/32 (N=%d), full" % w2.size]
+    t_op = {k: w2.size ** 2 / v for k, v in r2.items()}
+    for row in c2rows:
+        nd, ns = row["fp32c_local_steps"]
+        sweeps = row["outer_its"] + 2
+        row["oracle_s_extrapolated"] = (nd * t_op["laplace_DL"] + ns * t_op["stokes_DL"]
+                                        + sweeps * (t_op["laplace_SL"] + t_op["stokes_SL"]))
+    baseline = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "headline ellipsoid: " + sample, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                "single_thread": rate1,
+                "operator_rates_pairs_per_s": rates,
+                "ddm_time_to_solution_s": {"C1 sphere h=1/8 porous-sphere benchmark (kappa=1, theta=0.75, "
+                                           "interface GMRES 1e-9), run in full": c1_s,
+                                           "C1_outer_its": r1["outer_its"],
+                                           "C2 rows": "oracle_s_extrapolated in each sphere row (per-operator "
+                                                      "time x the device solve's operator counts)"}}
+
+    # checks of the device's results with the oracle
+    checks = {}
+    for row in c2rows:
+        kap, gam = row["kappa"], row["alpha"]
+        q, pd, u, f = A.bjs_interface_fields(xyz2, 1.0, kap, gam, 1.0, (0.0, 0.0, 1.0))
+        d = A.bjs_drag(1.0, kap, gam, 1.0, 1.0)
+        for tag in ("fp32c", "fp64"):
+            res = row.pop("_" + tag, None)
+            if res is None:
+                continue
+            row["vs_closed_form_" + tag] = {
+                "drag_rel": (res["drag"][2] - d) / d,
+                "p_rel_rms": S.rms(res["p"] - pd) / S.rms(pd),
+                "u_rms_over_U": S.rms(res["u"] - u),
+                "q_rms_over_U": S.rms(res["q"] - q)}
+    # the ellipsoid solution in the oracle's operators on sampled rows:
+    # Darcy  -D^L p - (mu/kappa) L q = 0 (p has zero weighted mean),
+    # Stokes u - D^S u + M f - U_inf + n (w.(u.n))/sum(w) = 0
+    rows = np.arange(0, w5.size, 1024)
+    qv, pv, uv, fv = c5["_q"], c5["_p"], c5["_u"], c5["_f"]
+    tg = xyz5[:, rows]
+    bD = (1.0 / KAPPA5) * oracle.laplace_sl(pts5, 3 * H5, qv, targets=tg)
+    rD = -oracle.laplace_dl(pts5, 3 * H5, pv, rows=rows) - bD
+    Mf = oracle.stokes_sl(pts5, 3 * H5, 1.0, fv, targets=tg)
+    flux = float(w5 @ (uv * nrm5).sum(0)) / float(w5.sum())
+    rS = uv[:, rows] - oracle.stokes_dl(pts5, 3 * H5, uv, rows=rows) + Mf - np.array([0.0, 0.0, 1.0])[:, None] \
+        + flux * nrm5[:, rows]
+    checks["ellipsoid_oracle_residual"] = {
+        "rows": "every 1024th target (%d rows x %d sources)" % (rows.size, w5.size),
+        "darcy_rel": float(np.linalg.norm(rD) / np.linalg.norm(bD)),
+        "stokes_rel": float(np.linalg.norm(rS) / np.linalg.norm(Mf)),
+        "q_minus_u_dot_n_rel": float(np.linalg.norm(qv - (uv * nrm5).sum(0)) / np.linalg.norm(qv))}
+    return baseline, checks
 
 
 def run_reference(args):
@@ -173,14 +297,14 @@ def run_reference(args):
     import oracle
     from oracle import quadrature as Q
     oracle.build()
-    pts = Q.sphere_points(1.0, H)
+    pts = Q.ellipsoid_points(ABC5, H5)
     for _ in range(args.warmup):
-        oracle_pair_rate(0.0, pts["xyz"], pts["nrm"], pts["w"], 3 * H)
+        oracle_sample_rate(0.0, pts, 3 * H5)
     t0 = time.perf_counter()
     pairs = 0.0
-    info = None
+    sample = None
     for _ in range(args.steps):
-        rate, info = oracle_pair_rate(0.0, pts["xyz"], pts["nrm"], pts["w"], 3 * H)
+        _, sample = oracle_sample_rate(0.0, pts, 3 * H5)
         pairs += 2.0 * len(range(0, pts["w"].size, 64)) * pts["w"].size
     el = time.perf_counter() - t0
     value = pairs / el
@@ -188,8 +312,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                             "sample": "per step: " + info["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "per step: " + sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -208,6 +332,10 @@ def combine_ranks(ms, pairs, dist, device):
     return float(t.item()), float(pt.item())
 
 
+def _pairs(ctx, prec):
+    return sum(ctx.kernel_stats(c, prec)["pairs"] for c in range(6))
+
+
 def run_ours(args):
     import torch
     import paper_2110_10749_gb300 as ssd
@@ -223,33 +351,41 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ctx = ssd.Context(local)
-    # inputs: quadrature points generated on the device (our kernel)
-    q = ssd.quadrature_points(ctx, ssd.SPHERE, (1.0,), H)
-    P = ssd.Points(q["xyz"], q["nrm"], q["w"]).prepare(ctx)
-    n = P.n
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def one_step(prec):
-        outs = []
-        for kappa in KAPPAS:
-            for alpha in ALPHAS:
-                outs.append(ssd.ddm_solve(ctx, P, ddm_prm(ssd, kappa, alpha, prec), raise_on_notconv=False))
-        return outs
+    # ---------------------------------------------------------------- C5
+    g5 = ssd.quadrature_points(ctx, ssd.ELLIPSOID, ABC5, H5)
+    P5 = ssd.Points(g5["xyz"], g5["nrm"], g5["w"]).prepare(ctx)
+    n5 = P5.n
+    prm5 = ddm_prm(ssd, H5, KAPPA5, GAMMA5, ssd.FP32C)
+    # the whole D-N solve: time-to-solution (device events)
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sol = ssd.ddm_solve(ctx, P5, prm5, raise_on_notconv=False)
+    e1.record(stream)
+    e1.synchronize()
+    tts_ms = e0.elapsed_time(e1)
+    tts_pairs = _pairs(ctx, ssd.FP32C)
+    ctx.set_timing(False)
+    inner = np.array(sol["inner_its"], dtype=np.int64).reshape(-1, 2)
+    zq = sol["q"].clone()
+    zu = sol["u"].clone()
+    c5 = {"status": sol["status"], "outer_its": sol["outer_its"],
+          "final_interface_residual": sol["hist"][-1] if sol["hist"] else None,
+          "fp32c_time_to_solution_ms": tts_ms, "pairs": tts_pairs,
+          "pairs_per_s": tts_pairs / (tts_ms / 1e3),
+          "local_gmres_steps": {"darcy": int(inner[:, 0].sum()), "stokes": int(inner[:, 1].sum()),
+                                "max_darcy": int(inner[:, 0].max()), "max_stokes": int(inner[:, 1].max())},
+          "drag": [float(v) for v in sol["drag"]]}
 
-    # plain FP64 reference solves on the GPU (untimed for the metric; timed per solve)
-    fp64 = {}
-    if not args.skip_fp64:
-        for kappa in (KAPPAS if args.fp64_all else KAPPAS[:2]):
-            for alpha in ALPHAS:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r = ssd.ddm_solve(ctx, P, ddm_prm(ssd, kappa, alpha, ssd.FP64), raise_on_notconv=False)
-                torch.cuda.synchronize()
-                fp64[(kappa, alpha)] = (r, time.perf_counter() - t0)
+    # timed steps: D-N sweeps from the converged state
+    out5 = {k: torch.empty_like(v) for k, v in (("q", zq), ("p", zq), ("u", zu), ("f", zu))}
     for _ in range(args.warmup):
-        one_step(ssd.FP32C)
-    # timed region
+        ssd.ddm_sweep(ctx, P5, prm5, zq, zu, out=out5, raise_on_notconv=False)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -259,25 +395,14 @@ def run_ours(args):
     sampler.start()
     l0 = ctx.launch_count()
     total_ms = 0.0
-    per_solve = []
-    last = None
     for _ in range(args.steps):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        outs = []
-        for kappa in KAPPAS:
-            for alpha in ALPHAS:
-                s0 = torch.cuda.Event(enable_timing=True)
-                s1 = torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
-                outs.append(ssd.ddm_solve(ctx, P, ddm_prm(ssd, kappa, alpha, ssd.FP32C), raise_on_notconv=False))
-                s1.record(stream)
-                per_solve.append((s0, s1, kappa, alpha))
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        last = outs
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ssd.ddm_sweep(ctx, P5, prm5, zq, zu, out=out5, raise_on_notconv=False)
+        s1.record(stream)
+        s1.synchronize()
+        total_ms += s0.elapsed_time(s1)
     torch.cuda.synchronize()
     launches = ctx.launch_count() - l0
     clocks = sampler.stop()
@@ -286,91 +411,120 @@ def run_ours(args):
     pairs_total = sum(s["pairs"] for s in stats.values())
     total_ms, pairs_all = combine_ranks(total_ms, pairs_total, dist, dev)
     value = pairs_all / (total_ms / 1e3)
+    # the sweep's own fixed-point residual at the FP32C solution
+    c5["fp32c_sweep_fixed_point_residual_q"] = float(torch.linalg.norm(out5["q"] - zq) / torch.linalg.norm(zq))
 
-    # time-to-solution and FP32C-vs-FP64 errors per solve
-    tts = {}
-    for (s0, s1, kappa, alpha) in per_solve:
-        tts.setdefault((kappa, alpha), []).append(s0.elapsed_time(s1))
-    solves = []
-    for k, (kappa, alpha) in enumerate([(a, b) for a in KAPPAS for b in ALPHAS]):
-        r32 = last[k]
-        row = {"kappa": kappa, "alpha": alpha, "status": r32["status"], "outer_its": r32["outer_its"],
-               "outer_relres": r32["hist"][0] if r32["hist"] else None,
-               "fp32c_ms": statistics.median(tts[(kappa, alpha)]), "drag_z": float(r32["drag"][2])}
-        if (kappa, alpha) in fp64:
-            r64, t64 = fp64[(kappa, alpha)]
-            row["fp64_ms"] = 1e3 * t64
-            row["fp64_outer_its"] = r64["outer_its"]
-            row["fp64_status"] = r64["status"]
-            for key in ("q", "p", "u", "f"):
-                a, b = r32[key], r64[key]
-                row["relerr_%s" % key] = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-            # velocity against the far-field speed (the surface velocity is ~kappa U)
-            row["err_u_vs_U"] = float(torch.linalg.norm(r32["u"] - r64["u"]) / math.sqrt(n))
-        solves.append(row)
-
-    # dominant kernel: the fused/Stokes double layer (FP32C) -- roofline against FP32 peak
+    # roofline of the dominant kernel in the timed sweeps (algorithmic flops)
     dom_cls = max(stats, key=lambda c: stats[c]["ms"])
     dom = stats[dom_cls]
-    names = ["laplace_SL", "laplace_DL", "stokes_SL", "stokes_DL", "stokes_SLDL", "laplace_SLDL"]
-    xyz_h = q["xyz"].cpu().numpy()
-    fnear = near_fraction(xyz_h, 3 * H)
-    flops_pair = FLOPS_SDL_FAR * (1 - fnear) + FLOPS_SDL_NEAR * fnear
-    if dom_cls == ssd.K_STOKES_SLDL:
-        flops_pair += 15  # single-layer terms shared with the double layer pass
+    xyz5_h = g5["xyz"].cpu().numpy()
+    fnear = near_fraction(xyz5_h, 3 * H5)
+    far, near = FLOPS[dom_cls]
+    flops_pair = far * (1 - fnear) + near * fnear
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak = sms * 128 * 2 * 2070e6 / 1e12
     achieved = dom["pairs"] * flops_pair / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
-    # DRAM bytes (read + write) per launch of the fused Stokes kernel on this
-    # workload, from one ncu capture (the sources stay in L2 between launches)
-    traffic = DRAM_BYTES_SSLDL if dom_cls == ssd.K_STOKES_SLDL else None
-    roofline = {"bound": "alu", "kernel": "pair32_kernel<%s> (FP32C, packed f32x2)" % names[dom_cls],
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "flops_per_pair": flops_pair, "near_fraction": fnear,
+    roofline = {"bound": "alu", "kernel": "pair32_kernel<%s> (FP32C)" % KNAMES[dom_cls],
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": DRAM_BYTES.get(dom_cls), "flops_per_pair": flops_pair,
+                "flops_per_pair_far_near": [far, near], "near_fraction": fnear,
                 "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(dom["launches"], 1),
                 "share_of_step": dom["ms"] / total_ms if total_ms > 0 else None,
-                "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 flop x 2070 MHz (unit counts and max clock)"
-                             % sms}
+                "peak_note": "FP32 FMA peak = %d SMs x 128 lanes x 2 flop x 2070 MHz (unit counts and max clock; "
+                             "MEASURED_PEAKS.json has no FP32 figure)" % sms}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside
-    xyz_p = q["xyz"].cpu().pin_memory()
-    nrm_p = q["nrm"].cpu().pin_memory()
-    w_p = q["w"].cpu().pin_memory()
-    outs_h = [{"q": torch.empty(n, dtype=torch.float64).pin_memory(),
-               "p": torch.empty(n, dtype=torch.float64).pin_memory(),
-               "u": torch.empty((3, n), dtype=torch.float64).pin_memory(),
-               "f": torch.empty((3, n), dtype=torch.float64).pin_memory()} for _ in range(6)]
-    e2e_ms = 0.0
-    e2e_steps = max(1, min(args.steps, 3))
-    ctx.reset_stats()
-    ctx.set_timing(True)
-    for _ in range(e2e_steps):
+    # plain FP64 on the GPU at the headline size: one sweep from the FP32C
+    # solution (its fixed-point residual measures the FP32C solution in FP64
+    # arithmetic) and the FP64 sweep time
+    if not args.skip_fp64:
+        prm64 = ddm_prm(ssd, H5, KAPPA5, GAMMA5, ssd.FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o64 = ssd.ddm_sweep(ctx, P5, prm64, zq, zu, raise_on_notconv=False)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        c5["fp64_sweep_ms"] = 1e3 * t64
+        c5["fp64_sweep_local_steps"] = list(o64["inner_its"])
+        c5["fp64_fixed_point_residual_q"] = float(torch.linalg.norm(o64["q"] - zq) / torch.linalg.norm(zq))
+        c5["fp64_fixed_point_residual_u"] = float(torch.linalg.norm(o64["u"] - zu) / torch.linalg.norm(zu))
+        c5["fp32c_vs_fp64_sweep_p"] = float(torch.linalg.norm(out5["p"] - o64["p"]) / torch.linalg.norm(o64["p"]))
+        c5["fp64_time_to_solution_ms_extrapolated"] = 1e3 * t64 * (sol["outer_its"] + 2)
+        c5["fp64_note"] = ("one plain-FP64 sweep from the FP32C solution; the FP64 solve time is that sweep's "
+                           "time x the FP32C solve's sweep count (a full FP64 solve at this size takes about an hour)")
+
+    # end to end: the whole solve through the host-buffer C entry point
+    xyz_p = g5["xyz"].cpu().pin_memory()
+    nrm_p = g5["nrm"].cpu().pin_memory()
+    w_p = g5["w"].cpu().pin_memory()
+    out_h = {"q": torch.empty(n5, dtype=torch.float64).pin_memory(),
+             "p": torch.empty(n5, dtype=torch.float64).pin_memory(),
+             "u": torch.empty((3, n5), dtype=torch.float64).pin_memory(),
+             "f": torch.empty((3, n5), dtype=torch.float64).pin_memory()}
+    e2e = None
+    if not args.skip_e2e:
+        ctx.reset_stats()
+        ctx.set_timing(True)
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        k = 0
-        for kappa in KAPPAS:
-            for alpha in ALPHAS:
-                ssd.ddm_solve_host(ctx, xyz_p, nrm_p, w_p, ddm_prm(ssd, kappa, alpha, ssd.FP32C), out=outs_h[k],
-                                   raise_on_notconv=False)
-                k += 1
+        rh = ssd.ddm_solve_host(ctx, xyz_p, nrm_p, w_p, prm5, out=out_h, raise_on_notconv=False)
         torch.cuda.synchronize()
-        e2e_ms += 1e3 * (time.perf_counter() - t0)
-    ctx.set_timing(False)
-    e2e_pairs = sum(ctx.kernel_stats(c, ssd.FP32C)["pairs"] for c in range(6))
-    e2e_ms, e2e_pairs = combine_ranks(e2e_ms, e2e_pairs, dist, dev)
-    e2e = {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": 6 * 7 * n * 8, "d2h_bytes_per_step": 6 * 8 * n * 8,
-           "note": "ssd_ddm_solve_host per solve: host->device copy of the points, layout build, "
-                   "solve, device->host copy of q, p, u, f"}
+        e2e_ms = 1e3 * (time.perf_counter() - t0)
+        ctx.set_timing(False)
+        e2e_pairs = _pairs(ctx, ssd.FP32C)
+        e2e_ms, e2e_pairs = combine_ranks(e2e_ms, e2e_pairs, dist, dev)
+        e2e = {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 7 * n5 * 8, "d2h_bytes_per_step": 8 * n5 * 8, "ms": e2e_ms,
+               "status": rh["status"], "outer_its": rh["outer_its"],
+               "note": "one whole headline D-N solve through ssd_ddm_solve_host (pinned host buffers): "
+                       "host->device copy of the points, layout build, solve, device->host copy of q, p, u, f"}
 
-    cpu = None
+    # ------------------------------------------------------- sphere section
+    g2 = ssd.quadrature_points(ctx, ssd.SPHERE, (1.0,), H2)
+    P2 = ssd.Points(g2["xyz"], g2["nrm"], g2["w"]).prepare(ctx)
+    c2rows = []
+    for kappa in KAPPAS:
+        for alpha in ALPHAS:
+            row = {"kappa": kappa, "alpha": alpha}
+            for prec, tag in ((ssd.FP32C, "fp32c"), (ssd.FP64, "fp64")):
+                if prec == ssd.FP64 and args.skip_fp64:
+                    continue
+                reps = 2 if prec == ssd.FP32C else 1
+                for _ in range(reps):    # FP32C: the second run is timed warm
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    r = ssd.ddm_solve(ctx, P2, ddm_prm(ssd, H2, kappa, alpha, prec), raise_on_notconv=False)
+                    b.record(stream)
+                    b.synchronize()
+                inn = np.array(r["inner_its"], dtype=np.int64).reshape(-1, 2)
+                row[tag + "_status"] = r["status"]
+                row[tag + "_outer_its"] = r["outer_its"]
+                row[tag + "_ms"] = a.elapsed_time(b)
+                row[tag + "_local_steps"] = [int(inn[:, 0].sum()), int(inn[:, 1].sum())]
+                row[tag + "_drag_z"] = float(r["drag"][2])
+                row["_" + tag] = {k: r[k].cpu().numpy() for k in ("q", "p", "u", "f")}
+                row["_" + tag]["drag"] = r["drag"]
+            row["outer_its"] = row["fp32c_outer_its"]
+            if "_fp64" in row:
+                for key in ("p", "u", "f"):
+                    a, b = row["_fp32c"][key], row["_fp64"][key]
+                    row["fp32c_vs_fp64_%s" % key] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                row["fp32c_vs_fp64_q_rms_over_U"] = float(np.sqrt(((row["_fp32c"]["q"] - row["_fp64"]["q"]) ** 2)
+                                                                  .mean()))
+            c2rows.append(row)
+
+    cpu, checks = None, None
     if rank == 0 and not args.skip_cpu:
-        nrm_h, w_h = q["nrm"].cpu().numpy(), q["w"].cpu().numpy()
-        rate, info = oracle_pair_rate(args.cpu_seconds, xyz_h, nrm_h, w_h, 3 * H)
-        cpu = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
-               "single_thread": oracle_single_thread_rate(0.25 * args.cpu_seconds, xyz_h, nrm_h, w_h, 3 * H)}
+        c5["_q"], c5["_p"] = sol["q"].cpu().numpy(), sol["p"].cpu().numpy()
+        c5["_u"], c5["_f"] = sol["u"].cpu().numpy(), sol["f"].cpu().numpy()
+        cpu, checks = oracle_leg(args, c5, c2rows, xyz5_h, g5["nrm"].cpu().numpy(), g5["w"].cpu().numpy(),
+                                 g2["xyz"].cpu().numpy(), g2["nrm"].cpu().numpy(), g2["w"].cpu().numpy())
+    for key in ("_q", "_p", "_u", "_f"):
+        c5.pop(key, None)
+    for row in c2rows:
+        row.pop("_fp32c", None)
+        row.pop("_fp64", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -379,10 +533,11 @@ def run_ours(args):
                 "precision": "FP32 pair terms with compensated accumulation; FP64 Krylov, interface and epilogue",
                 "data": "synthetic", "config": workload_config(), "clocks": clocks, "gpu_launches": launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "kernels": {names[c]: stats[c] for c in stats if stats[c]["launches"]},
-                "solves": solves}
+                "kernels": {KNAMES[c]: stats[c] for c in stats if stats[c]["launches"]},
+                "headline_solve": c5, "oracle_checks": checks, "sphere_h32_solves": c2rows}
         print(json.dumps(line), flush=True)
-    P.release()
+    P5.release()
+    P2.release()
     ctx.close()
     if dist:
         dist.destroy_process_group()
@@ -392,13 +547,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU comparison solves")
-    ap.add_argument("--fp64-all", action="store_true",
-                    help="FP64 comparison for all six solves (kappa = 1e-4 takes minutes); default kappa >= 1e-2")
-    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the plain FP64 GPU comparisons")
+    ap.add_argument("--skip-e2e", action="store_true", help="skip the end-to-end host-buffer solve")
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the oracle leg (CPU baseline and checks)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.impl == "reference":

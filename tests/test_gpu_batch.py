@@ -1,6 +1,8 @@
 """Batched launches over several surfaces (uneven point counts, one smoothing
 radius each) and several right-hand sides, against the oracle surface by
 surface and against the single-surface device path."""
+import math
+
 import numpy as np
 import pytest
 
@@ -127,3 +129,61 @@ def test_batch_argument_errors(gpu_ctx, batch):
     prm = ssd.ddm_params(kappa=1.0, gamma=1.0, outer_gmres=True, traction_mode=ssd.TRACTION_BJS, bjs_implicit=False)
     with pytest.raises(ssd.SsdError):
         ssd.batch_ddm_solve(gpu_ctx, B, prm, [[0, 0, 1.0]])  # lagged BJS is not batched
+
+
+def test_batched_star_surfaces_of_the_batched_workload(gpu_ctx):
+    """Star surfaces of the batched workload's recipe (c_lm ~ N(0, 0.05^2),
+    seeds 0 and 3) and an ellipsoid (1, 0.8, 0.6), all at h = 1/24,
+    5e3-1e4 points each, in one batch: operators against the oracle on
+    sampled rows, and the batched D-N solve against single-surface solves."""
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    from paper_2110_10749_gb300.workloads import star_coefficients
+    spec = [("star", star_coefficients(0), 1 / 24), ("star", star_coefficients(3), 1 / 24),
+            ("ell", (1.0, 0.8, 0.6), 1 / 24)]
+    pts = [Q.star_points(c, h) if kind == "star" else Q.ellipsoid_points(c, h) for kind, c, h in spec]
+    sizes = [p["w"].size for p in pts]
+    assert min(sizes) >= 5000, sizes
+    deltas = [3 * h for _, _, h in spec]
+    B = ssd.Batch.from_numpy(pts, deltas).prepare(gpu_ctx)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    n = offs[-1]
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=(2, 1, n))
+    v = rng.normal(size=(2, 3, n))
+    tg, tv = torch.as_tensor(g, device="cuda"), torch.as_tensor(v, device="cuda")
+    for prec, tol in ((ssd.FP64, 1e-12), (ssd.FP32C, 1e-5)):
+        oL = ssd.batch_apply(gpu_ctx, B, ssd.OP_LAPLACE_DL, tg, prec=prec).cpu().numpy()
+        oS = ssd.batch_apply(gpu_ctx, B, ssd.OP_STOKES_DL, tv, prec=prec).cpu().numpy()
+        oM = ssd.batch_apply(gpu_ctx, B, ssd.OP_STOKES_SL, tv, mu=1.0, prec=prec).cpu().numpy()
+        for r in range(2):
+            for s, p in enumerate(pts):
+                sl = slice(offs[s], offs[s + 1])
+                rows = np.arange(0, sizes[s], 41)
+                refL = oracle.laplace_dl(p, deltas[s], g[r, 0, sl], rows=rows)
+                refS = oracle.stokes_dl(p, deltas[s], v[r][:, sl], rows=rows)
+                refM = oracle.stokes_sl(p, deltas[s], 1.0, v[r][:, sl], targets=p["xyz"][:, rows])
+                for got, ref in ((oL[r, 0, sl][rows], refL), (oS[r][:, sl][:, rows], refS),
+                                 (oM[r][:, sl][:, rows], refM)):
+                    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, (prec, r, s)
+    uinf = np.array([[0.0, 0.0, 1.0], [1.0 / math.sqrt(3.0)] * 3])
+    kappa, gamma = 1e-2, 1.0
+    inner = ssd.krylov(1e-9, 200, 200, False, ssd.FP32C, deflate=True)
+    prm = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=gamma, theta=0.5 * kappa, tol_outer=1e-8, maxit_outer=100,
+                         outer_gmres=True, traction_mode=ssd.TRACTION_BJS, bjs_implicit=True, inner=inner)
+    rb = ssd.batch_ddm_solve(gpu_ctx, B, prm, uinf)
+    assert rb["status"] == ssd.SSD_OK
+    for r in range(2):
+        for s, p in enumerate(pts):
+            sl = slice(offs[s], offs[s + 1])
+            P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
+            prm1 = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=gamma, uinf=tuple(uinf[r]), delta=deltas[s],
+                                  theta=0.5 * kappa, tol_outer=1e-8, maxit_outer=100, outer_gmres=True,
+                                  traction_mode=ssd.TRACTION_BJS, bjs_implicit=True, inner=inner)
+            r1 = ssd.ddm_solve(gpu_ctx, P, prm1)
+            P.release()
+            for k in ("p", "u"):
+                a = rb[k][r][..., sl].cpu().numpy().reshape(r1[k].shape)
+                b = r1[k].cpu().numpy()
+                assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5, (k, r, s)
+    B.release()

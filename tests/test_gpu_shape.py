@@ -166,3 +166,53 @@ def test_shape_autograd(gpu_ctx):
     assert abs(out.item() - J) <= 1e-12 * abs(J)
     assert np.allclose(c.grad.numpy(), dc, rtol=1e-12, atol=0)
     assert abs(lk.grad.item() - g[0]) <= 1e-12 * abs(g[0])
+
+
+def test_config4_size_gradients_device_fd(gpu_ctx):
+    """The differentiation workload at its own size: the unit sphere at
+    h = 1/32 (N = 17070), drag and flux moment differentiated in log(kappa)
+    and gamma, and the drag in three shape coefficients, by the adjoint,
+    against Richardson-
+    extrapolated central differences of device FP64 solves (the oracle would
+    take minutes per solve at this size)."""
+    import paper_2110_10749_gb300 as ssd
+    h = 1 / 32
+    clm = np.zeros(25)
+    kappa, gamma = 1e-2, 1.0
+    prm = _prm(ssd, h, kappa, gamma)
+
+    def Jd(c, k, gm, func):
+        q = ssd.quadrature_points(gpu_ctx, ssd.STAR, h=h, clm=c)
+        P = ssd.Points(q["xyz"], q["nrm"], q["w"]).prepare(gpu_ctx)
+        pr = _prm(ssd, h, k, gm)
+        r = ssd.ddm_solve(gpu_ctx, P, pr)
+        if func == ssd.FUNC_DRAG:
+            v = float(r["drag"][2])
+        else:
+            v = float((q["w"] * r["q"] * q["xyz"][2]).sum())
+        P.release()
+        return v
+
+    def rich(f, x0, eps):
+        d1 = (f(x0 + eps) - f(x0 - eps)) / (2 * eps)
+        d2 = (f(x0 + eps / 2) - f(x0 - eps / 2)) / eps
+        return (4.0 * d2 - d1) / 3.0
+
+    for func in (ssd.FUNC_DRAG, ssd.FUNC_FLUX):
+        J, g, dc, st = ssd.ddm_shape_gradient(gpu_ctx, clm, h, prm, func)
+        assert st == ssd.SSD_OK
+        assert abs(J - Jd(clm, kappa, gamma, func)) <= 1e-10 * abs(J)
+        fk = rich(lambda lk: Jd(clm, math.exp(lk), gamma, func), math.log(kappa), 2e-3)
+        fg = rich(lambda gm: Jd(clm, kappa, gm, func), gamma, 2e-3)
+        assert abs(g[0] - fk) <= 1e-6 * abs(fk), (func, g[0], fk)
+        assert abs(g[1] - fg) <= 1e-6 * abs(fg), (func, g[1], fg)
+        if func == ssd.FUNC_FLUX:
+            continue
+        scale = np.abs(dc).max()
+        for k in (0, 6, 20):
+            def fc(e, k=k):
+                c = clm.copy()
+                c[k] = e
+                return Jd(c, kappa, gamma, func)
+            fd = rich(fc, 0.0, 2e-4)
+            assert abs(dc[k] - fd) <= 1e-6 * scale, (func, k, dc[k], fd)
