@@ -91,6 +91,12 @@ int ssd_ctx_reset_stats(ssd_ctx *ctx);
 /* Total kernel launches the library issued since the context was created
  * (every kernel of the library, not only the pair sums). */
 int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out /* host */);
+/* Measurement aid (the paper has no counterpart): the FP32 FMA rate this
+ * device reaches, in TFLOP/s (FMA = 2 flops), from a kernel that keeps 16
+ * independent FMA chains per thread on every SM (packed = 1: as f32x2
+ * FFMA2 instructions, the form the pair kernels use; 0: scalar FFMA).
+ * Synchronises the device's legacy stream. */
+int ssd_fp32_fma_rate(ssd_ctx *ctx, int packed, double *tflops /* host */);
 
 /* ------------------------------------------------------------- quadrature */
 
@@ -330,6 +336,11 @@ typedef struct {
     double bjs_sign;           /* s in the BJS traction: +1 (default) or -1 */
     double radius;             /* sphere radius R (JOSEPH_TAO mode; sphere centred at 0) */
     ssd_krylov inner;          /* local solves; inner.tol applies to both */
+    int refine;                /* FP32C interface GMRES only: up to this many refinement
+                                  steps, each taking the true residual F(z) - z from one
+                                  plain-FP64 sweep and solving D (I - G) e = D r for the
+                                  correction with FP32C sweeps; the returned fields are
+                                  those of the last FP64 sweep.  0 = off */
 } ssd_ddm_params;
 
 /*

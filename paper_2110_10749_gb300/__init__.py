@@ -33,6 +33,7 @@ K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_S
 EXPORTS = [
     "ssd_ctx_create", "ssd_ctx_destroy", "ssd_status_string", "ssd_ctx_last_error",
     "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count",
+    "ssd_fp32_fma_rate",
     "ssd_quadrature_points", "ssd_quadrature_jacobian", "ssd_points_prepare", "ssd_points_release",
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
     "ssd_stokes_SLDL", "ssd_laplace_SLDL", "ssd_apply_rows", "ssd_points_order",
@@ -80,7 +81,8 @@ class CDdmParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("kappa", C.c_double), ("gamma", C.c_double), ("uinf", C.c_double * 3),
                 ("delta", C.c_double), ("theta", C.c_double), ("tol_outer", C.c_double),
                 ("maxit_outer", C.c_int), ("outer_gmres", C.c_int), ("traction_mode", C.c_int),
-                ("bjs_implicit", C.c_int), ("bjs_sign", C.c_double), ("radius", C.c_double), ("inner", CKrylov)]
+                ("bjs_implicit", C.c_int), ("bjs_sign", C.c_double), ("radius", C.c_double), ("inner", CKrylov),
+                ("refine", C.c_int)]
 
 
 class BatchLayoutC(C.Structure):
@@ -122,6 +124,7 @@ def lib():
         "ssd_ctx_kernel_stats": [P, i, i, C.POINTER(CKernelStats)],
         "ssd_ctx_reset_stats": [P],
         "ssd_ctx_launch_count": [P, C.POINTER(i64)],
+        "ssd_fp32_fma_rate": [P, i, C.POINTER(d)],
         "ssd_quadrature_points": [P, C.POINTER(CSurface), d, d, i64, C.POINTER(i64), P, P, P, P, P],
         "ssd_quadrature_jacobian": [P, C.POINTER(CSurface), d, d, i64, P, P, P, P],
         "ssd_points_prepare": [P, C.POINTER(CPoints), P],
@@ -254,6 +257,12 @@ class Context:
 
     def reset_stats(self):
         self.check(lib().ssd_ctx_reset_stats(self.h), "ssd_ctx_reset_stats")
+
+    def fp32_fma_rate(self, packed=True):
+        """Measured FP32 FMA rate of the device in TFLOP/s (FMA = 2 flops)."""
+        v = C.c_double()
+        self.check(lib().ssd_fp32_fma_rate(self.h, 1 if packed else 0, C.byref(v)), "ssd_fp32_fma_rate")
+        return v.value
 
     def launch_count(self):
         v = C.c_int64()
@@ -470,10 +479,10 @@ def stokes_solve(ctx, pts, delta, mu, f, uinf, kr=None, out=None):
 
 def ddm_params(mu=1.0, kappa=1.0, gamma=0.0, uinf=(0.0, 0.0, 1.0), delta=0.1, theta=0.5, tol_outer=1e-9,
                maxit_outer=100, outer_gmres=False, traction_mode=TRACTION_BJS, bjs_sign=1.0, radius=1.0,
-               inner=None, bjs_implicit=False):
+               inner=None, bjs_implicit=False, refine=0):
     return CDdmParams(float(mu), float(kappa), float(gamma), (C.c_double * 3)(*uinf), float(delta), float(theta),
                       float(tol_outer), int(maxit_outer), 1 if outer_gmres else 0, int(traction_mode),
-                      1 if bjs_implicit else 0, float(bjs_sign), float(radius), inner or krylov())
+                      1 if bjs_implicit else 0, float(bjs_sign), float(radius), inner or krylov(), int(refine))
 
 
 def _ddm_out(prm, n, dev):

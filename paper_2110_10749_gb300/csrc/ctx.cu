@@ -487,6 +487,7 @@ void release_layout(ssd_ctx *ctx, Layout *L) {
     if (L->block) dev_free(ctx, L->block);
     for (int k = 0; k < 2; ++k)
         if (L->order32[k]) dev_free(ctx, L->order32[k]);
+    if (L->sym_block) dev_free(ctx, L->sym_block);
     *L = Layout();
 }
 
@@ -622,6 +623,7 @@ int ssd_ctx_create(ssd_ctx **out, int device) {
     }
     // tuning knob: 0 launches the FP32C grid in plain (tile, split) order
     if (const char *w = getenv("SSD_PAIR_LPT")) ctx->lpt = atoi(w) != 0;
+    if (const char *w = getenv("SSD_PAIR_SYM")) ctx->sym = atoi(w) != 0;
     if (const char *w = getenv("SSD_PAIR_WAVES64")) {
         const int v = atoi(w);
         if (v >= 1 && v <= 64) ctx->waves64 = v;
@@ -740,3 +742,68 @@ int ssd_quadrature_jacobian(ssd_ctx *ctx, const ssd_surface *surf, double h, dou
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- FP32 FMA rate (measurement)
+// Every thread keeps 16 independent FMA chains (8 packed f32x2 pairs, or 16
+// scalars) for `iters` steps; the result is stored only when it equals a
+// value it cannot reach, so nothing is optimised away.  Used to measure the
+// FP32 rate the pair kernels can reach on this device.
+namespace ssd {
+namespace {
+__global__ void __launch_bounds__(256) fma_rate_kernel(int packed, int iters, float m, float c, float *sink) {
+    if (packed) {
+        float2 a[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = make_float2(threadIdx.x * 1e-3f + k, blockIdx.x * 1e-3f - k);
+        const float2 mm = make_float2(m, m), cc = make_float2(c, c);
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = __ffma2_rn(a[k], mm, cc);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += a[k].x + a[k].y;
+        if (s == -12345.678f) sink[0] = s;
+    } else {
+        float a[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = threadIdx.x * 1e-3f + k;
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = fmaf(a[k], m, c);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) s += a[k];
+        if (s == -12345.678f) sink[0] = s;
+    }
+}
+}  // namespace
+}  // namespace ssd
+
+extern "C" int ssd_fp32_fma_rate(ssd_ctx *ctx, int packed, double *tflops) {
+    using namespace ssd;
+    if (!ctx || !tflops) return SSD_EINVAL;
+    ctx->err.clear();
+    void *sink = nullptr;
+    SSD_TRY(dev_alloc(ctx, 256, &sink));
+    struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } release{ctx, sink};
+    const int blocks = ctx->num_sms * 8, threads = 256, iters = 1 << 14;
+    cudaEvent_t e0, e1;
+    SSD_TRY(cuda_check(ctx, cudaEventCreate(&e0), "event"));
+    SSD_TRY(cuda_check(ctx, cudaEventCreate(&e1), "event"));
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {   // the last of three launches is timed
+        cudaEventRecord(e0, 0);
+        fma_rate_kernel<<<blocks, threads, 0, 0>>>(packed, iters, 0.999999f, 1e-7f, static_cast<float *>(sink));
+        cudaEventRecord(e1, 0);
+        ctx->launches++;
+    }
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SSD_TRY(cuda_check(ctx, e, "fma rate kernel"));
+    const double fmas = (double)blocks * threads * iters * 16.0;
+    *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+    return SSD_OK;
+}

@@ -734,6 +734,9 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     int its = 0;
     int status = SSD_OK;
     std::vector<double> hist;
+    Ddm D64;                        // FP64 sweeps of the refinement (unused otherwise)
+    D64.ctx = nullptr;
+    const double *fsrc = nullptr;   // traction of the returned state
     if (!prm->outer_gmres) {
         // relaxed sweeps; z = (q, u_prev) with u_prev kept in z + n
         for (its = 1; its <= prm->maxit_outer; ++its) {
@@ -788,17 +791,65 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
         // the lagged BJS interface needs a few hundred steps at small kappa and
         // large gamma; a restart there stalls, so the cycle is as long as allowed
         const int m_out = prm->maxit_outer < kMaxRestart ? prm->maxit_outer : kMaxRestart;
+        // with refinement the FP32C solve only needs to get below the pair-sum
+        // rounding (about 1e-7 relative); the FP64 residuals take it further
+        const bool refine = prm->refine > 0 && prm->inner.prec == SSD_FP32C;
+        const double tol1 = refine && prm->tol_outer < 1e-6 ? 1e-6 : prm->tol_outer;
         // each matvec is a whole sweep: no step is queued ahead of its check
-        int st = gmres(ctx, s, nz, F, cs.d(), z.d(), prm->tol_outer, m_out, prm->maxit_outer, false, &gr, false,
-                       &hist);
+        int st = gmres(ctx, s, nz, F, cs.d(), z.d(), tol1, m_out, prm->maxit_outer, false, &gr, false, &hist);
         if (st == SSD_ENOTCONV) status = SSD_ENOTCONV;
         else SSD_TRY(st);
         its = gr.iters;
         if (!stacked) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(z.d() + n, 0, sizeof(double) * 3 * n, s), "memset"));
-        // final sweep from the solution gives the returned fields
-        SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
-        SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(z.d() + n, zn.d() + n, sizeof(double) * 3 * n,
-                                                cudaMemcpyDeviceToDevice, s), "copy"));
+        if (!refine) {
+            // final sweep from the solution gives the returned fields
+            SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(z.d() + n, zn.d() + n, sizeof(double) * 3 * n,
+                                                    cudaMemcpyDeviceToDevice, s), "copy"));
+        } else {
+            // iterative refinement: r = F64(z) - z is the true residual of
+            // (I - G) z = c, from one plain-FP64 sweep; D (I - G) e = D r is
+            // solved with the FP32C sweeps and z += e
+            D64.ctx = ctx; D64.pts = pts; D64.L = lref.L; D64.P = *prm; D64.P.inner.prec = SSD_FP64;
+            D64.P.outer_gmres = 1; D64.s = s; D64.n = n;
+            SSD_TRY(D64.f.alloc(ctx, sizeof(double) * 3 * n));
+            Buf rb, eb;
+            SSD_TRY(rb.alloc(ctx, sizeof(double) * 4 * n));
+            SSD_TRY(eb.alloc(ctx, sizeof(double) * 4 * n));
+            SSD_TRY(dots.multi(cs.d(), 0, 1, cs.d(), nz, D.scal.d()));
+            double hc[1];
+            SSD_TRY(read_scalars(ctx, D.scal.d(), 1, hc, s));
+            const double cnorm = sqrt(hc[0]);
+            for (int k = 0;; ++k) {
+                SSD_TRY(D64.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
+                SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(rb.d(), zn.d(), sizeof(double) * nz, cudaMemcpyDeviceToDevice,
+                                                        s), "copy"));
+                axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, -1.0, z.d(), 1.0, rb.d());   // F64(z) - z
+                ctx->launches++;
+                if (stacked) {
+                    axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 0.0, rb.d(), qscale, rb.d());
+                    ctx->launches++;
+                }
+                SSD_TRY(dots.multi(rb.d(), 0, 1, rb.d(), nz, D.scal.d()));
+                SSD_TRY(read_scalars(ctx, D.scal.d(), 1, hc, s));
+                const double rel = cnorm > 0.0 ? sqrt(hc[0]) / cnorm : 0.0;
+                if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite refinement residual");
+                hist.push_back(rel);
+                if (rel <= prm->tol_outer) { status = SSD_OK; break; }
+                if (k >= prm->refine) { status = SSD_ENOTCONV; break; }
+                GmresResult ge;
+                const double tcorr = fmax(0.5 * prm->tol_outer / rel, 1e-4);
+                st = gmres(ctx, s, nz, F, rb.d(), eb.d(), tcorr, m_out, prm->maxit_outer, false, &ge, false, &hist);
+                if (st != SSD_ENOTCONV) SSD_TRY(st);
+                its += ge.iters;
+                axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, 1.0, eb.d(), 1.0, z.d());
+                ctx->launches++;
+            }
+            // the returned fields are those of the last FP64 sweep
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(z.d() + n, zn.d() + n, sizeof(double) * 3 * n,
+                                                    cudaMemcpyDeviceToDevice, s), "copy"));
+            fsrc = D64.f.d();
+        }
     }
     // outputs: q (the interface variable at convergence), p_D, u_S, f_S
     if (q_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(q_out, z.d(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
@@ -807,10 +858,11 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
                                   "copy"));
     if (u_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u_out, z.d() + n, sizeof(double) * 3 * n,
                                                        cudaMemcpyDeviceToDevice, s), "copy"));
-    if (f_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(f_out, D.f.d(), sizeof(double) * 3 * n,
+    if (!fsrc) fsrc = D.f.d();
+    if (f_out) SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(f_out, fsrc, sizeof(double) * 3 * n,
                                                        cudaMemcpyDeviceToDevice, s), "copy"));
     // drag = sum_x w f (eq. drag_int)
-    SSD_TRY(dots.multi(D.f.d(), n, 3, pts->w, n, D.scal.d()));
+    SSD_TRY(dots.multi(fsrc, n, 3, pts->w, n, D.scal.d()));
     double dh[3];
     SSD_TRY(read_scalars(ctx, D.scal.d(), 3, dh, s));
     if (drag) for (int k = 0; k < 3; ++k) drag[k] = dh[k];
@@ -821,7 +873,8 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
     }
     if (res_hist)
         for (size_t k = 0; k < hist.size() && k < (size_t)prm->maxit_outer; ++k) res_hist[k] = hist[k];
-    if (D.nonconv && status == SSD_OK) status = SSD_ENOTCONV;
+    if (D64.ctx && D64.nonconv && status == SSD_OK) status = SSD_ENOTCONV;
+    if (D.nonconv && status == SSD_OK && !D64.ctx) status = SSD_ENOTCONV;
     if (status == SSD_ENOTCONV) set_error(ctx, SSD_ENOTCONV, "iteration limit reached in the D-N solve");
     return status;
 }

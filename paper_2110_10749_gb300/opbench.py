@@ -27,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--prec", default="fp32c", choices=["fp32c", "fp64"])
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--peak", action="store_true", help="also measure the FP32 FMA rate (FFMA and FFMA2)")
     args = ap.parse_args(argv)
 
     import torch
@@ -55,6 +56,12 @@ def main(argv=None):
         "laplace_SLDL": lambda: ssd.laplace_SLDL(ctx, P, delta, g, g, 1.0, -1.0, prec),
     }
     cls = dict(zip(OPS, range(6)))
+    if args.peak:
+        props = torch.cuda.get_device_properties(0)
+        for packed in (0, 1):
+            print(json.dumps({"fp32_fma_rate_tflops": ctx.fp32_fma_rate(bool(packed)),
+                              "form": "FFMA2 (f32x2)" if packed else "FFMA", "sms": props.multi_processor_count}),
+                  flush=True)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     for name in args.ops.split(","):
         for _ in range(args.warmup):
