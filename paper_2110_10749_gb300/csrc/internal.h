@@ -57,6 +57,14 @@ struct Layout {
     int2 *order32[2] = {nullptr, nullptr};
     int64_t order_nit[2] = {0, 0}, order_chunk[2] = {0, 0};
     float order_rfar2[2] = {-1.f, -1.f};
+    // plan of the FP32C double layers that evaluates far block pairs once for
+    // both directions (prepared layouts only), cached for the last
+    // rho_far delta it was built for: near items (pair32 items) and far items
+    // (symmetric kernel) in one device block
+    void *sym_block = nullptr;
+    int64_t sym_near = 0, sym_far = 0;
+    float sym_rfar2 = -1.f;
+    bool sym_use = false;
 };
 
 struct TimedLaunch {
@@ -77,6 +85,7 @@ struct ssd_ctx {
     int occ32 = 1, occ64 = 1;  // resident CTAs per SM of the pair kernels
     int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
     int lpt = 1;               // pair grids in near-first order on prepared layouts
+    int sym = 1;               // FP32C double layers: far block pairs once for both directions
     int waves64 = 8;           // FP64 grid: about this many waves of resident CTAs (tuned)
     void *noalloc_scratch = nullptr;   // device address of the no-alloc scratch array (first no-alloc call)
     std::string err;

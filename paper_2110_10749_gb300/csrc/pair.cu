@@ -371,6 +371,8 @@ struct K32Args {
     const int2 *order = nullptr;
     int nslot = 2;
     int64_t tile0 = 0;          // single-surface launch without order: first target tile
+    double *acc = nullptr;      // items of one surface: add (hi + lo) to acc[c][i] atomically
+                                // instead of writing per-split partials
 };
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
@@ -639,10 +641,162 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
         const int64_t i = tbase + threadIdx.x + t * kTPB32;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
+            if (a.acc) {
+                atomicAdd(a.acc + q * a.n_pad + i, (double)hi[t][q] + (double)lo[t][q]);
+                continue;
+            }
             float *dst = a.part + part_base + (int64_t)(q * a.nslot) * pstride + i;
             dst[0] = hi[t][q];
             if (a.nslot == 2) dst[pstride] = lo[t][q];
         }
+    }
+}
+
+// ------------------------------------------------- symmetric far block pairs
+// The double layers evaluated once per unordered pair of points in two
+// blocks of the layout that are farther apart than rho_far delta (bare
+// kernels, s_i = 1).  For targets a and sources b with yh = y_a - x_b, and
+// m = w n:
+//   Stokes:  A = (yh . (u_b - u_a)) / r^5,
+//            a <- A (yh . m_b) yh,   b <- A (yh . m_a) yh
+//   Laplace: B = (p_b - p_a) / r^3,
+//            a <- B (yh . m_b),      b <- B (yh . m_a)
+// (the reverse terms follow from yh -> -yh and swapping the roles), so r, its
+// powers and the density difference are shared by both directions.
+// A CTA holds 512 targets (4 per thread) of one block and walks source tiles
+// of 128 staged in shared memory.  At step s lane l takes source
+// (l + s) mod 128, so the 32 lanes of a warp work on 32 different sources and
+// add their reverse terms to the warp's own shared accumulator without
+// conflict; after the tile the four warps' accumulators are summed.  Forward
+// sums fold per tile into (hi, lo) pairs; both directions end in an FP64
+// atomic add to acc[c][point].
+struct SymItem {
+    int32_t tb, s0, s1, pad;   // targets [tb, tb + 512), sources [s0, s1) (whole tiles)
+};
+
+struct SymArgs {
+    const float4 *pos, *wn, *d0;
+    const SymItem *items;
+    int64_t n_pad;
+    double *acc;               // [NC][n_pad]
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs a) {
+    constexpr int NC = OpInfo<OP>::NC;
+    constexpr int NP = kTPT32 / 2;
+    constexpr int NW = kTPB32 / 32;
+    static_assert(kTile == kTPB32, "one staged source per thread");
+    __shared__ float4 sm_pos[kTile], sm_wn[kTile], sm_d0[kTile];
+    __shared__ float4 sm_rev[NW][kTile];
+    const SymItem it = a.items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2 y[NP][3], dt[NP][3], tm[NP][3];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int64_t i0 = it.tb + threadIdx.x + (2 * k) * kTPB32, i1 = i0 + kTPB32;
+        const float4 p0 = a.pos[i0], p1 = a.pos[i1];
+        const float4 e0 = a.d0[i0], e1 = a.d0[i1];
+        const float4 m0 = a.wn[i0], m1 = a.wn[i1];
+        y[k][0] = make_float2(p0.x, p1.x); y[k][1] = make_float2(p0.y, p1.y); y[k][2] = make_float2(p0.z, p1.z);
+        dt[k][0] = make_float2(e0.x, e1.x); dt[k][1] = make_float2(e0.y, e1.y); dt[k][2] = make_float2(e0.z, e1.z);
+        tm[k][0] = make_float2(m0.x, m1.x); tm[k][1] = make_float2(m0.y, m1.y); tm[k][2] = make_float2(m0.z, m1.z);
+    }
+    float hi[kTPT32][NC], lo[kTPT32][NC];
+#pragma unroll
+    for (int t = 0; t < kTPT32; ++t)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hi[t][q] = lo[t][q] = 0.f;
+
+    for (int64_t tile = it.s0; tile < it.s1; tile += kTile) {
+        __syncthreads();
+        sm_pos[threadIdx.x] = a.pos[tile + threadIdx.x];
+        sm_wn[threadIdx.x] = a.wn[tile + threadIdx.x];
+        sm_d0[threadIdx.x] = a.d0[tile + threadIdx.x];
+#pragma unroll
+        for (int q = 0; q < NW; ++q) sm_rev[q][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        float2 part[NP][NC];
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+#pragma unroll
+            for (int q = 0; q < NC; ++q) part[k][q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int st = 0; st < kTile; ++st) {
+            const int j = (lane + st) & (kTile - 1);
+            const float4 sp = sm_pos[j], sw = sm_wn[j], s0 = sm_d0[j];
+            float2 rv[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) rv[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float2 dx = sub2(y[k][0], bc2(sp.x)), dy = sub2(y[k][1], bc2(sp.y)), dz = sub2(y[k][2], bc2(sp.z));
+                const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                const float2 ri = rsq2(r2);
+                const float2 ri2 = mul2(ri, ri);
+                const float2 ynb = fma2(dz, bc2(sw.z), fma2(dy, bc2(sw.y), mul2(dx, bc2(sw.x))));
+                const float2 yna = fma2(dz, tm[k][2], fma2(dy, tm[k][1], mul2(dx, tm[k][0])));
+                if (OP == OP_SDL) {
+                    const float2 ux = sub2(bc2(s0.x), dt[k][0]), uy = sub2(bc2(s0.y), dt[k][1]),
+                                 uz = sub2(bc2(s0.z), dt[k][2]);
+                    const float2 du = fma2(uz, dz, fma2(uy, dy, mul2(ux, dx)));
+                    const float2 A = mul2(du, mul2(mul2(ri2, ri2), ri));
+                    const float2 f = mul2(A, ynb), g = mul2(A, yna);
+                    part[k][0] = fma2(f, dx, part[k][0]);
+                    part[k][1] = fma2(f, dy, part[k][1]);
+                    part[k][2] = fma2(f, dz, part[k][2]);
+                    rv[0] = fma2(g, dx, rv[0]);
+                    rv[1] = fma2(g, dy, rv[1]);
+                    rv[2] = fma2(g, dz, rv[2]);
+                } else {   // OP_LDL
+                    const float2 B = mul2(sub2(bc2(s0.x), dt[k][0]), mul2(ri2, ri));
+                    part[k][0] = fma2(B, ynb, part[k][0]);
+                    rv[0] = fma2(B, yna, rv[0]);
+                }
+            }
+            float4 acc4 = sm_rev[warp][j];
+            acc4.x += rv[0].x + rv[0].y;
+            if (NC == 3) {
+                acc4.y += rv[1 % NC].x + rv[1 % NC].y;
+                acc4.z += rv[2 % NC].x + rv[2 % NC].y;
+            }
+            sm_rev[warp][j] = acc4;
+            __syncwarp();
+        }
+        // forward: fold the tile's sums into the (hi, lo) pairs (TwoSum)
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    const int t = 2 * k + l;
+                    const float p = l ? part[k][q].y : part[k][q].x;
+                    const float sum = hi[t][q] + p;
+                    const float bp = sum - hi[t][q];
+                    lo[t][q] += (hi[t][q] - (sum - bp)) + (p - bp);
+                    hi[t][q] = sum;
+                }
+        // reverse: the four warps' sums of source tile + threadIdx.x
+        __syncthreads();
+        float4 r = sm_rev[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < NW; ++q) {
+            const float4 v = sm_rev[q][threadIdx.x];
+            r.x += v.x; r.y += v.y; r.z += v.z;
+        }
+        const int64_t jb = tile + threadIdx.x;
+        atomicAdd(a.acc + jb, (double)r.x);
+        if (NC == 3) {
+            atomicAdd(a.acc + a.n_pad + jb, (double)r.y);
+            atomicAdd(a.acc + 2 * a.n_pad + jb, (double)r.z);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kTPT32; ++t) {
+        const int64_t i = it.tb + threadIdx.x + t * kTPB32;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) atomicAdd(a.acc + q * a.n_pad + i, (double)hi[t][q] + (double)lo[t][q]);
     }
 }
 
@@ -1100,6 +1254,129 @@ int item_order(ssd_ctx *ctx, const Layout &L, int slot, int tpb, int tpt, int64_
     return SSD_OK;
 }
 
+// Work lists of the symmetric plan of the FP32C double layers (see
+// sym32_kernel), built once per prepared layout and rho_far delta from the
+// chunk boxes.  Blocks of 512 points: a pair of blocks whose boxes (of their
+// real points) are farther apart than rho_far delta goes to the symmetric
+// kernel, in items of the target block against at most kSymTiles source
+// tiles; the diagonal blocks and the near block pairs (both directions) are
+// items of pair32_kernel.  The plan is used when far pairs are at least half
+// of all pairs.
+constexpr int kSymBlock = kTPB32 * kTPT32;
+constexpr int kSymTiles = 8;
+
+int sym_plan(ssd_ctx *ctx, const Layout &L, const Consts<float> &c, cudaStream_t s) {
+    Layout &M = const_cast<Layout &>(L);
+    if (M.sym_rfar2 == c.rfar2) return SSD_OK;
+    if (M.sym_block) { dev_free(ctx, M.sym_block); M.sym_block = nullptr; }
+    M.sym_use = false;
+    M.sym_near = M.sym_far = 0;
+    const int64_t n = L.n, n_pad = L.n_pad, nb = n_pad / kSymBlock, nch = n_pad / kChunk;
+    std::vector<float4> cb(2 * nch);
+    SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(cb.data(), L.cbox, sizeof(float4) * 2 * nch, cudaMemcpyDeviceToHost, s),
+                       "chunk box copy"));
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "chunk box sync"));
+    // boxes of the real points of each block
+    std::vector<float> blo(3 * nb, 1e30f), bhi(3 * nb, -1e30f);
+    for (int64_t ch = 0; ch < nch && ch * kChunk < n; ++ch) {
+        const int64_t b = ch * kChunk / kSymBlock;
+        const float lo[3] = {cb[2 * ch].x, cb[2 * ch].y, cb[2 * ch].z};
+        const float hi[3] = {cb[2 * ch + 1].x, cb[2 * ch + 1].y, cb[2 * ch + 1].z};
+        for (int q = 0; q < 3; ++q) {
+            blo[3 * b + q] = fminf(blo[3 * b + q], lo[q]);
+            bhi[3 * b + q] = fmaxf(bhi[3 * b + q], hi[q]);
+        }
+    }
+    auto far_pair = [&](int64_t i, int64_t k) {
+        if (blo[3 * i] > bhi[3 * i] || blo[3 * k] > bhi[3 * k]) return true;   // a block of padding only
+        double g2 = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double g = fmax(0.0, fmax((double)blo[3 * k + q] - bhi[3 * i + q], (double)blo[3 * i + q] - bhi[3 * k + q]));
+            g2 += g * g;
+        }
+        return g2 >= (double)c.rfar2;
+    };
+    std::vector<BItem> near;
+    std::vector<SymItem> far;
+    int64_t far_blocks = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+        near.push_back(BItem{(int32_t)(i * kSymBlock), (int32_t)(i * kSymBlock), (int32_t)((i + 1) * kSymBlock),
+                             0, 0, 0, 0, 0});
+        int64_t k = i + 1;
+        while (k < nb) {
+            if (!far_pair(i, k)) {
+                near.push_back(BItem{(int32_t)(i * kSymBlock), (int32_t)(k * kSymBlock),
+                                     (int32_t)((k + 1) * kSymBlock), 0, 0, 0, 0, 0});
+                near.push_back(BItem{(int32_t)(k * kSymBlock), (int32_t)(i * kSymBlock),
+                                     (int32_t)((i + 1) * kSymBlock), 0, 0, 0, 0, 0});
+                ++k;
+                continue;
+            }
+            int64_t k1 = k;
+            while (k1 < nb && far_pair(i, k1)) ++k1;
+            far_blocks += k1 - k;
+            for (int64_t t = k * kSymBlock; t < k1 * kSymBlock; t += (int64_t)kSymTiles * kTile) {
+                int64_t e = t + (int64_t)kSymTiles * kTile;
+                if (e > k1 * kSymBlock) e = k1 * kSymBlock;
+                far.push_back(SymItem{(int32_t)(i * kSymBlock), (int32_t)t, (int32_t)e, 0});
+            }
+            k = k1;
+        }
+    }
+    M.sym_rfar2 = c.rfar2;
+    // far pairs (both directions) against all ordered pairs
+    if (2.0 * (double)far_blocks < 0.5 * (double)nb * (double)nb) return SSD_OK;
+    size_t off = 0;
+    auto carve = [&](size_t b) { size_t o = off; off += (b + 255) & ~size_t(255); return o; };
+    const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(sizeof(Consts<float>));
+    const size_t o_near = carve(sizeof(BItem) * near.size()), o_far = carve(sizeof(SymItem) * far.size());
+    void *blk = nullptr;
+    SSD_TRY(dev_alloc(ctx, off, &blk));
+    char *b = static_cast<char *>(blk);
+    const BSurf sf{0, n_pad, n, 0, 1, 0, 0, 0};
+    std::vector<char> host(off);
+    memcpy(host.data() + o_surf, &sf, sizeof(sf));
+    memcpy(host.data() + o_c, &c, sizeof(c));
+    memcpy(host.data() + o_near, near.data(), sizeof(BItem) * near.size());
+    memcpy(host.data() + o_far, far.data(), sizeof(SymItem) * far.size());
+    const int st = cuda_check(ctx, cudaMemcpyAsync(b, host.data(), off, cudaMemcpyHostToDevice, s), "plan copy");
+    if (st == SSD_OK) SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "plan sync"));
+    if (st != SSD_OK) { dev_free(ctx, blk); return st; }
+    M.sym_block = blk;
+    M.sym_near = (int64_t)near.size();
+    M.sym_far = (int64_t)far.size();
+    M.sym_use = true;
+    return SSD_OK;
+}
+
+template <int OP>
+cudaError_t launch_sym(const Layout &L, const float4 *d0, double *acc, cudaStream_t s) {
+    char *b = static_cast<char *>(L.sym_block);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(sizeof(Consts<float>));
+    const size_t o_near = carve(sizeof(BItem) * L.sym_near);
+    const size_t o_far = carve(sizeof(SymItem) * L.sym_far);
+    K32Args ka;
+    ka.pos = L.pos32; ka.wn = L.wn32; ka.cbox = L.cbox; ka.d0 = d0; ka.d1 = d0;
+    ka.n = L.n; ka.n_pad = L.n_pad; ka.chunk = kSymBlock;
+    ka.part = nullptr;
+    ka.items = reinterpret_cast<const BItem *>(b + o_near);
+    ka.surfs = reinterpret_cast<const BSurf *>(b + o_surf);
+    ka.consts = reinterpret_cast<const Consts<float> *>(b + o_c);
+    ka.rec_stride = 0; ka.part_stride = 0;
+    ka.acc = acc;
+    pair32_kernel<OP><<<dim3((unsigned)L.sym_near, 1), kTPB32, 0, s>>>(ka);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.sym_far == 0) return e;
+    SymArgs sa;
+    sa.pos = L.pos32; sa.wn = L.wn32; sa.d0 = d0;
+    sa.items = reinterpret_cast<const SymItem *>(b + o_far);
+    sa.n_pad = L.n_pad; sa.acc = acc;
+    sym32_kernel<OP><<<(unsigned)L.sym_far, kTPB32, 0, s>>>(sa);
+    return cudaGetLastError();
+}
+
 int pair_occupancy(ssd_ctx *ctx) {
     int o32 = 0, o64 = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o32, pair32_kernel<OP_SSLDL>, kTPB32, 0);
@@ -1147,6 +1424,15 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const size_t o_d1 = two_rec ? carve(rec * n_pad) : 0;
     const size_t o_part = carve(rsz * nslot * nc * nsplit * n_pad);
     const size_t o_wdot = carve(sizeof(double) * pack_blocks);
+    // FP32C double layers on a prepared layout: the symmetric plan when far
+    // block pairs are most of the work (FP64 accumulator instead of partials)
+    const bool rows_req = pc.row_end >= 0;
+    bool use_sym = false;
+    if (packed32 && (op == OP_SDL || op == OP_LDL) && !rows_req && ctx->sym && L.order_ok) {
+        SSD_TRY(sym_plan(ctx, L, make_consts<float>(pc.delta, kRhoFar32), s));
+        use_sym = L.sym_use;
+    }
+    const size_t o_acc = use_sym ? carve(sizeof(double) * nc * n_pad) : 0;
     void *ws = nullptr;
     SSD_TRY(dev_alloc(ctx, off, &ws));
     struct Release { ssd_ctx *c; void *p; ~Release() { dev_free(c, p); } } release{ctx, ws};
@@ -1199,10 +1485,17 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     if (rows && !(pc.row_begin >= 0 && pc.row_begin < pc.row_end && pc.row_end <= n))
         return set_error(ctx, SSD_EINVAL, "row block must satisfy 0 <= row_begin < row_end <= n");
     cudaEvent_t ev = nullptr;
+    double *acc = use_sym ? reinterpret_cast<double *>(base + o_acc) : nullptr;
+    if (use_sym)
+        SSD_TRY(cuda_check(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * nc * n_pad, s), "accumulator memset"));
     SSD_TRY(timed_begin(ctx, s, &ev));
     dim3 grid((unsigned)(tile1 - tile0), (unsigned)nsplit);
     cudaError_t e;
-    if (f32 && transposed) {
+    if (use_sym) {
+        const float4 *d0 = reinterpret_cast<const float4 *>(base + o_d0);
+        e = op == OP_SDL ? launch_sym<OP_SDL>(L, d0, acc, s) : launch_sym<OP_LDL>(L, d0, acc, s);
+        if (L.sym_far) ctx->launches++;   // near items and far items: two launches
+    } else if (f32 && transposed) {
         KArgs<float> ka;
         ka.pos = L.pos32; ka.wn = L.wn32;
         ka.d0 = reinterpret_cast<const float4 *>(base + o_d0);
@@ -1261,6 +1554,9 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     EpiArgs ea{};
     ea.perm = L.perm; ea.n = n; ea.n_pad = n_pad; ea.nc = nc; ea.nsplit = (int)nsplit; ea.nslot = nslot;
     ea.part_is_float = f32 ? 1 : 0; ea.part = base + o_part;
+    if (use_sym) {   // one FP64 sum per point and component
+        ea.nsplit = 1; ea.nslot = 1; ea.part_is_float = 0; ea.part = acc;
+    }
     ea.scale = scale; ea.self_coef = self_coef; ea.self_src = self_src; ea.pos64 = L.pos64;
     ea.xin = pc.xin; ea.a_id = pc.a_id; ea.a_op = pc.a_op;
     ea.add0 = pc.add[0]; ea.add1 = pc.add[1]; ea.add2 = pc.add[2]; ea.add_dev = pc.add_dev;
