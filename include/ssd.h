@@ -359,8 +359,10 @@ typedef struct {
  *   inner_its[2 * max(maxit_outer + 2, 1)] = (Darcy, Stokes) iterations per sweep,
  *   res_hist[maxit_outer] = DDM residual per sweep (SA) or the interface
  *   GMRES residual estimate ||D (c - (I - G) z_k)|| / ||D c|| after each step k
- *   (GMRES; one cycle of up to min(maxit_outer, 512) steps, then restarts).
- *   Host pointers may be NULL.
+ *   (GMRES; one cycle of up to min(maxit_outer, 512) steps, then restarts),
+ *   followed, with refine, by the FP64 residual ||D (F(z) - z)|| / ||D c|| of
+ *   each refinement step; an entry of -1 ends the history when it is shorter
+ *   than maxit_outer.  Host pointers may be NULL.
  * Synchronises `stream`.
  */
 int ssd_ddm_solve(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,

@@ -493,6 +493,16 @@ def _ddm_out(prm, n, dev):
             "f": torch.empty((3, n), dtype=torch.float64, device=dev)}
 
 
+def _history(hist, cap):
+    """The entries of a residual history up to its -1 end mark."""
+    out = []
+    for k in range(max(cap, 1)):
+        if hist[k] < 0.0:
+            break
+        out.append(hist[k])
+    return out
+
+
 def ddm_solve(ctx, pts, prm, raise_on_notconv=True):
     """Dirichlet-Neumann solve (Sections 3, 6).  Returns a dict of results."""
     o = _ddm_out(prm, pts.n, pts.xyz.device)
@@ -509,7 +519,7 @@ def ddm_solve(ctx, pts, prm, raise_on_notconv=True):
     o["outer_its"] = oits.value
     n_sweeps = oits.value + 2 if prm.outer_gmres else oits.value
     o["inner_its"] = [(inner[2 * k], inner[2 * k + 1]) for k in range(min(n_sweeps, cap // 2))]
-    o["hist"] = list(hist[:min(oits.value, prm.maxit_outer)])
+    o["hist"] = _history(hist, prm.maxit_outer)
     o["status"] = st
     return o
 

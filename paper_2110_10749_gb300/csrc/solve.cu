@@ -642,14 +642,16 @@ struct Ddm {
     Buf f, scal;
     std::vector<int> inner;   // (darcy, stokes) per sweep
     int nonconv = 0;
+    bool start_from_outputs = false;   // local solves start from the contents of p and u
 
     // one sweep: (q, uprev) -> (qn, u); p and f are left in pbuf and f
     int sweep(const double *q, const double *uprev, double *qn, double *u, double *p) {
         GmresResult rd, rs;
         // relaxed sweeps may start each local solve from the previous sweep's
-        // solution (p keeps it; u starts from uprev)
-        const bool warm = P.inner.warm && !P.outer_gmres;
-        if (warm && u != uprev)
+        // solution (p keeps it; u starts from uprev); the refinement's FP64
+        // sweeps start from an FP32C sweep's solutions already in p and u
+        const bool warm = (P.inner.warm && !P.outer_gmres) || start_from_outputs;
+        if (warm && !start_from_outputs && u != uprev)
             SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u, uprev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s),
                                "warm start copy"));
         int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s, true, warm);
@@ -811,7 +813,7 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
             // (I - G) z = c, from one plain-FP64 sweep; D (I - G) e = D r is
             // solved with the FP32C sweeps and z += e
             D64.ctx = ctx; D64.pts = pts; D64.L = lref.L; D64.P = *prm; D64.P.inner.prec = SSD_FP64;
-            D64.P.outer_gmres = 1; D64.s = s; D64.n = n;
+            D64.P.outer_gmres = 1; D64.s = s; D64.n = n; D64.start_from_outputs = true;
             SSD_TRY(D64.f.alloc(ctx, sizeof(double) * 3 * n));
             Buf rb, eb;
             SSD_TRY(rb.alloc(ctx, sizeof(double) * 4 * n));
@@ -821,6 +823,8 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
             SSD_TRY(read_scalars(ctx, D.scal.d(), 1, hc, s));
             const double cnorm = sqrt(hc[0]);
             for (int k = 0;; ++k) {
+                // an FP32C sweep from z gives the FP64 local solves their start
+                SSD_TRY(D.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
                 SSD_TRY(D64.sweep(z.d(), z.d() + n, zn.d(), zn.d() + n, p.d()));
                 SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(rb.d(), zn.d(), sizeof(double) * nz, cudaMemcpyDeviceToDevice,
                                                         s), "copy"));
@@ -839,7 +843,7 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
                 if (k >= prm->refine) { status = SSD_ENOTCONV; break; }
                 GmresResult ge;
                 const double tcorr = fmax(0.5 * prm->tol_outer / rel, 1e-4);
-                st = gmres(ctx, s, nz, F, rb.d(), eb.d(), tcorr, m_out, prm->maxit_outer, false, &ge, false, &hist);
+                st = gmres(ctx, s, nz, F, rb.d(), eb.d(), tcorr, m_out, prm->maxit_outer, false, &ge, false);
                 if (st != SSD_ENOTCONV) SSD_TRY(st);
                 its += ge.iters;
                 axpby_kernel<<<grid_for(nz), 256, 0, s>>>(nz, 1.0, eb.d(), 1.0, z.d());
@@ -871,8 +875,11 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
         const size_t cap = 2 * (size_t)(prm->maxit_outer + 2);
         for (size_t k = 0; k < D.inner.size() && k < cap; ++k) inner_its[k] = D.inner[k];
     }
-    if (res_hist)
-        for (size_t k = 0; k < hist.size() && k < (size_t)prm->maxit_outer; ++k) res_hist[k] = hist[k];
+    if (res_hist) {
+        size_t k = 0;
+        for (; k < hist.size() && k < (size_t)prm->maxit_outer; ++k) res_hist[k] = hist[k];
+        if (k < (size_t)prm->maxit_outer) res_hist[k] = -1.0;   // end of the history
+    }
     if (D64.ctx && D64.nonconv && status == SSD_OK) status = SSD_ENOTCONV;
     if (D.nonconv && status == SSD_OK && !D64.ctx) status = SSD_ENOTCONV;
     if (status == SSD_ENOTCONV) set_error(ctx, SSD_ENOTCONV, "iteration limit reached in the D-N solve");
