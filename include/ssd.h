@@ -398,6 +398,19 @@ int ssd_ddm_solve_host(ssd_ctx *ctx, int64_t n, const double *xyz, const double 
                        int *inner_its, double *res_hist, ssd_stream stream);
 
 /*
+ * Columns of the discrete iteration matrix of the D-N sweeps (eq. A_mat,
+ * Section 6) assembled by its definition: column j of A~ is F(e_j) - F(0),
+ * F one sweep on the interface variable q (u_inf and the traction's constant
+ * part cancel in the difference).  Computes columns col0 .. col0 + ncol - 1
+ * into A (device, column-major n x ncol: A[k n + i] = (A~ e_{col0+k})_i).
+ * One sweep per column, in the precision of prm->inner.  The interface state
+ * must be q alone (SSD_EINVAL for the lagged slip with gamma != 0).
+ * Synchronises `stream`; SSD_ENOTCONV if a local solve reached its limit.
+ */
+int ssd_ddm_iteration_matrix(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm,
+                             int64_t col0, int64_t ncol, double *A, ssd_stream stream);
+
+/*
  * Spectrum of the discrete iteration matrix of the D-N sweeps (eq. A_mat,
  * Section 6; Fig. 5): m Arnoldi steps (Gram-Schmidt twice) on
  * A~ v = F(v) - F(0), F one relaxed sweep with prm's theta, from the start

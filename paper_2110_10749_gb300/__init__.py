@@ -42,6 +42,7 @@ EXPORTS = [
     "ssd_stokes_DL_noalloc", "ssd_apply_transpose", "ssd_ddm_gradient",
     "ssd_ddm_gradient_geometry", "ssd_geometry_gradient", "ssd_shape_contract",
     "ssd_darcy_pressure_field", "ssd_stokes_velocity_field", "ssd_stokes_pressure_field", "ssd_ddm_spectrum",
+    "ssd_ddm_iteration_matrix",
     "ssd_hessenberg_eigenvalues",
 ]
 OP_LAPLACE_SL, OP_LAPLACE_DL, OP_STOKES_SL, OP_STOKES_DL, OP_STOKES_SLDL, OP_LAPLACE_SLDL = range(6)
@@ -158,6 +159,7 @@ def lib():
                              C.POINTER(d), C.POINTER(d), P],
         "ssd_stokes_velocity_field": [P, C.POINTER(CPoints), d, C.POINTER(d), P, P, i64, P, P, P],
         "ssd_stokes_pressure_field": [P, C.POINTER(CPoints), d, P, P, i64, P, P, P],
+        "ssd_ddm_iteration_matrix": [P, C.POINTER(CPoints), C.POINTER(CDdmParams), i64, i64, P, P],
         "ssd_hessenberg_eigenvalues": [i, C.POINTER(d), i, C.POINTER(d), C.POINTER(d)],
         "ssd_batch_prepare": [P, C.POINTER(CBatch), P],
         "ssd_batch_release": [P, C.POINTER(CBatch)],
@@ -610,6 +612,20 @@ def ddm_spectrum(ctx, pts, prm, m=50):
     ritz = np.array(re[:k]) + 1j * np.array(im[:k])
     Hm = np.array(H[:]).reshape(m, m + 1).T[:k + 1, :k]
     return ritz, Hm
+
+
+def ddm_iteration_matrix(ctx, pts, prm, col0=0, ncol=None, out=None):
+    """Columns col0 .. col0 + ncol - 1 of the discrete iteration matrix
+    (eq. A_mat): CUDA tensor (n, ncol), column j = F(e_{col0+j}) - F(0)."""
+    torch = _torch()
+    n = pts.n
+    ncol = n - col0 if ncol is None else int(ncol)
+    if out is None:
+        out = torch.empty((ncol, n), dtype=torch.float64, device=pts.xyz.device)
+    ctx.check(lib().ssd_ddm_iteration_matrix(ctx.h, C.byref(pts.c), C.byref(prm), int(col0), ncol,
+                                             _arg(out, n * ncol, pts.xyz.device, "out"), _stream()),
+              "ssd_ddm_iteration_matrix")
+    return out.T
 
 
 def hessenberg_eigenvalues(H):

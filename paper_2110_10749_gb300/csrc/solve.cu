@@ -1078,6 +1078,51 @@ __global__ void golden_fill_kernel(int64_t n, double *v) {
 
 // Ritz values of the discrete iteration matrix A~ v = F(v) - F(0), F one D-N
 // sweep (eq. A_mat), from m Arnoldi steps (Gram-Schmidt twice).
+// e = unit vector of index j (length n)
+__global__ void unit_vector_kernel(int64_t n, int64_t j, double *e) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        e[k] = k == j ? 1.0 : 0.0;
+}
+
+// The discrete iteration matrix of eq. A_mat, column by column: column j is
+// F(e_j) - F(0) for the sweep F on the interface variable q.
+int ddm_iteration_matrix_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int64_t col0,
+                              int64_t ncol, double *A, cudaStream_t s) {
+    SSD_TRY(check_ddm(ctx, prm));
+    if (!A) return set_error(ctx, SSD_EINVAL, "NULL output");
+    if (!pts || col0 < 0 || ncol < 1 || col0 + ncol > pts->n)
+        return set_error(ctx, SSD_EINVAL, "columns must satisfy 0 <= col0 < col0 + ncol <= n");
+    if (prm->traction_mode == SSD_TRACTION_BJS && prm->gamma != 0.0 && !prm->bjs_implicit)
+        return set_error(ctx, SSD_EINVAL, "the iteration matrix acts on q alone: lagged slip with gamma != 0 "
+                                          "is not supported");
+    LayoutRef lref;
+    SSD_TRY(get_layout(ctx, pts, &lref, s));
+    Ddm D;
+    D.ctx = ctx; D.pts = pts; D.L = lref.L; D.P = *prm; D.P.outer_gmres = 1; D.s = s; D.n = pts->n;
+    const int64_t n = pts->n;
+    SSD_TRY(D.f.alloc(ctx, sizeof(double) * 3 * n));
+    Buf c, zero, e, u, p;
+    SSD_TRY(c.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(zero.alloc(ctx, sizeof(double) * 4 * n));
+    SSD_TRY(e.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(u.alloc(ctx, sizeof(double) * 3 * n));
+    SSD_TRY(p.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(cuda_check(ctx, cudaMemsetAsync(zero.d(), 0, sizeof(double) * 4 * n, s), "memset"));
+    SSD_TRY(D.sweep(zero.d(), zero.d() + n, c.d(), u.d(), p.d()));      // c = F(0)
+    const unsigned gb = grid_for(n);
+    for (int64_t j = 0; j < ncol; ++j) {
+        double *col = A + (size_t)j * n;
+        unit_vector_kernel<<<gb, 256, 0, s>>>(n, col0 + j, e.d());
+        ctx->launches++;
+        SSD_TRY(D.sweep(e.d(), zero.d() + n, col, u.d(), p.d()));
+        axpby_kernel<<<gb, 256, 0, s>>>(n, -1.0, c.d(), 1.0, col);     // F(e_j) - F(0)
+        ctx->launches++;
+    }
+    SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "iteration matrix sync"));
+    if (D.nonconv) return set_error(ctx, SSD_ENOTCONV, "a local solve reached its iteration limit");
+    return SSD_OK;
+}
+
 int ddm_spectrum_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m, int *m_out,
                       double *re, double *im, double *Hout, cudaStream_t s) {
     SSD_TRY(check_ddm(ctx, prm));
@@ -1762,6 +1807,13 @@ int ssd_ddm_sweep(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm
     if (!ctx) return SSD_EINVAL;
     ctx->err.clear();
     return ddm_sweep_impl(ctx, pts, prm, q, u_prev, q_out, p_D, u_S, f_S, inner_its, (cudaStream_t)stream);
+}
+
+int ssd_ddm_iteration_matrix(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int64_t col0,
+                             int64_t ncol, double *A, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    ctx->err.clear();
+    return ddm_iteration_matrix_impl(ctx, pts, prm, col0, ncol, A, (cudaStream_t)stream);
 }
 
 int ssd_ddm_spectrum(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, int m, int *m_out,

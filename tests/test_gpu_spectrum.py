@@ -37,3 +37,32 @@ def test_spectrum_matches_oracle(gpu_ctx, kappa, theta):
     a1 = (1 - theta) - theta / (3 * kappa)
     assert np.abs(a[:3] - a1).max() < 5e-3 * max(1.0, abs(a1))
     P.release()
+
+
+@pytest.mark.parametrize("kappa,theta", [(1.0, 0.5), (1e-2, 0.005)])
+def test_assembled_iteration_matrix_matches_oracle_definition(gpu_ctx, kappa, theta):
+    """A~ assembled on the device column by column from sweeps (FP64, and
+    FP32C) against the oracle's dense A~ of eq. A_mat, entry by entry, and
+    their eigenvalues."""
+    import paper_2110_10749_gb300 as ssd
+    h = 1 / 8
+    p = Q.sphere_points(1.0, h)
+    P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
+    Ao = S.iteration_matrix(p, 3 * h, 1.0, kappa, theta)
+    res = {}
+    for prec, tol_in in ((ssd.FP64, 1e-13), (ssd.FP32C, 1e-9)):
+        inner = ssd.krylov(tol_in, 300, 300, False, prec, False)
+        prm = ssd.ddm_params(mu=1.0, kappa=kappa, gamma=0.0, uinf=(0.0, 0.0, 1.0), delta=3 * h, theta=theta,
+                             tol_outer=1e-12, maxit_outer=80, outer_gmres=True, traction_mode=ssd.TRACTION_BJS,
+                             inner=inner)
+        res[prec] = ssd.ddm_iteration_matrix(gpu_ctx, P, prm).cpu().numpy()
+    scale = np.abs(Ao - (1 - theta) * np.eye(Ao.shape[0])).max()
+    assert np.abs(res[ssd.FP64] - Ao).max() < 1e-9 * scale
+    assert np.abs(res[ssd.FP32C] - Ao).max() < 1e-5 * scale
+    ev = np.sort(np.linalg.eigvals(res[ssd.FP64]).real)
+    evo = np.sort(np.linalg.eigvals(Ao).real)
+    assert np.abs(ev - evo).max() < 1e-8 * max(1.0, np.abs(evo).max())
+    # a block of columns equals the same columns of the whole matrix
+    blk = ssd.ddm_iteration_matrix(gpu_ctx, P, prm, col0=100, ncol=7).cpu().numpy()
+    assert np.abs(blk - res[ssd.FP32C][:, 100:107]).max() < 1e-12 * scale
+    P.release()
