@@ -687,8 +687,11 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
     constexpr int NP = kTPT32 / 2;
     constexpr int NW = kTPB32 / 32;
     static_assert(kTile == kTPB32, "one staged source per thread");
-    __shared__ float4 sm_pos[kTile], sm_wn[kTile], sm_d0[kTile];
-    __shared__ float4 sm_rev[NW][kTile];
+    // source records packed for the step loop: (x, y, z, d0.x), (w n, d0.y), d0.z;
+    // reverse sums one float per component, warp and source
+    __shared__ float4 sm_a[kTile], sm_b[kTile];
+    __shared__ float sm_c[NC == 3 ? kTile : 1];
+    __shared__ float sm_rev[NC][NW][kTile];
     const SymItem it = a.items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float2 y[NP][3], dt[NP][3], tm[NP][3];
@@ -710,11 +713,16 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
 
     for (int64_t tile = it.s0; tile < it.s1; tile += kTile) {
         __syncthreads();
-        sm_pos[threadIdx.x] = a.pos[tile + threadIdx.x];
-        sm_wn[threadIdx.x] = a.wn[tile + threadIdx.x];
-        sm_d0[threadIdx.x] = a.d0[tile + threadIdx.x];
+        {
+            const float4 ps = a.pos[tile + threadIdx.x], ms = a.wn[tile + threadIdx.x], ds = a.d0[tile + threadIdx.x];
+            sm_a[threadIdx.x] = make_float4(ps.x, ps.y, ps.z, ds.x);
+            sm_b[threadIdx.x] = make_float4(ms.x, ms.y, ms.z, ds.y);
+            if (NC == 3) sm_c[threadIdx.x] = ds.z;
+        }
 #pragma unroll
-        for (int q = 0; q < NW; ++q) sm_rev[q][threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < NC; ++q)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sm_rev[q][w][threadIdx.x] = 0.f;
         __syncthreads();
         float2 part[NP][NC];
 #pragma unroll
@@ -724,7 +732,8 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
 #pragma unroll 2
         for (int st = 0; st < kTile; ++st) {
             const int j = (lane + st) & (kTile - 1);
-            const float4 sp = sm_pos[j], sw = sm_wn[j], s0 = sm_d0[j];
+            const float4 sp = sm_a[j], sw = sm_b[j];
+            const float4 s0 = make_float4(sp.w, sw.w, NC == 3 ? sm_c[j] : 0.f, 0.f);
             float2 rv[NC];
 #pragma unroll
             for (int q = 0; q < NC; ++q) rv[q] = make_float2(0.f, 0.f);
@@ -754,13 +763,8 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
                     rv[0] = fma2(B, yna, rv[0]);
                 }
             }
-            float4 acc4 = sm_rev[warp][j];
-            acc4.x += rv[0].x + rv[0].y;
-            if (NC == 3) {
-                acc4.y += rv[1 % NC].x + rv[1 % NC].y;
-                acc4.z += rv[2 % NC].x + rv[2 % NC].y;
-            }
-            sm_rev[warp][j] = acc4;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) sm_rev[q][warp][j] += rv[q].x + rv[q].y;
             __syncwarp();
         }
         // forward: fold the tile's sums into the (hi, lo) pairs (TwoSum)
@@ -779,17 +783,13 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
                 }
         // reverse: the four warps' sums of source tile + threadIdx.x
         __syncthreads();
-        float4 r = sm_rev[0][threadIdx.x];
-#pragma unroll
-        for (int q = 1; q < NW; ++q) {
-            const float4 v = sm_rev[q][threadIdx.x];
-            r.x += v.x; r.y += v.y; r.z += v.z;
-        }
         const int64_t jb = tile + threadIdx.x;
-        atomicAdd(a.acc + jb, (double)r.x);
-        if (NC == 3) {
-            atomicAdd(a.acc + a.n_pad + jb, (double)r.y);
-            atomicAdd(a.acc + 2 * a.n_pad + jb, (double)r.z);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            float r = sm_rev[q][0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) r += sm_rev[q][w][threadIdx.x];
+            atomicAdd(a.acc + q * a.n_pad + jb, (double)r);
         }
     }
 #pragma unroll
