@@ -27,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["unit"] == "pair-interactions/s" and d["value"] > 0
     assert d["ms_per_step"] > 0
-    assert d["config"]["workload"] and d["config"]["n_points"] == 17070
+    assert d["config"]["workload"] and d["config"]["n_points"] == 138830
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
     assert cb["value"] == d["value"] and cb["unit"] == d["unit"]
