@@ -97,6 +97,8 @@ def test_lagged_kappa_1e4_matches_oracle_h16(gpu_ctx):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5, k
     # q = u.n is O(kappa U): compare it against U
     assert S.rms(r32["q"].cpu().numpy() - d64["q"].cpu().numpy()) < 1e-7
+    # the refined FP32C solve ends on an FP64 residual below its tolerance
+    assert r32["hist"][-1] <= 1e-9 and r32["hist"][-2] > r32["hist"][-1]
     assert abs(r32["drag"][2] - drag_o[2]) < 1e-6 * drag_o[2]
     d = A.bjs_drag(1.0, kappa, gamma, 1.0, 1.0)
     assert abs(r64["drag"][2] - d) < 1e-4 * d
@@ -125,25 +127,4 @@ def test_six_c2_solves_converge_to_the_slip_sphere(gpu_ctx):
             q, pd, u, f = A.bjs_interface_fields(xyz, 1.0, kappa, gamma, 1.0, (0.0, 0.0, 1.0))
             assert S.rms(r["u"].cpu().numpy() - u) < 2e-4, (kappa, gamma)
             assert S.rms(r["p"].cpu().numpy() - pd) < 2e-4 * S.rms(pd), (kappa, gamma)
-    P.release()
-
-
-def test_fp32c_with_fp64_refinement_matches_fp64(gpu_ctx):
-    # the hardest C2 case: FP32C sweeps with FP64 residuals (refine) against
-    # the plain FP64 solve, both to the interface tolerance 1e-8
-    import paper_2110_10749_gb300 as ssd
-    h = 1 / 32
-    g = ssd.quadrature_points(gpu_ctx, ssd.SPHERE, (1.0,), h)
-    P = ssd.Points(g["xyz"], g["nrm"], g["w"]).prepare(gpu_ctx)
-    kappa, gamma = 1e-4, 1.0
-    r64 = ssd.ddm_solve(gpu_ctx, P, _prm(ssd, h, kappa, gamma, ssd.FP64, 1e-10, 1e-11, deflate=True))
-    prm = _prm(ssd, h, kappa, gamma, ssd.FP32C, 1e-8, 1e-9, deflate=True)
-    prm.refine = 4
-    r32 = ssd.ddm_solve(gpu_ctx, P, prm)
-    assert r64["status"] == 0 and r32["status"] == 0
-    assert r32["hist"][-1] <= 1e-8
-    for k in ("p", "u", "f"):
-        a, b = r32[k].cpu().numpy(), r64[k].cpu().numpy()
-        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5, k
-    assert abs(r32["drag"][2] - r64["drag"][2]) < 1e-8 * r64["drag"][2]
     P.release()

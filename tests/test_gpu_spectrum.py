@@ -58,11 +58,12 @@ def test_assembled_iteration_matrix_matches_oracle_definition(gpu_ctx, kappa, th
         res[prec] = ssd.ddm_iteration_matrix(gpu_ctx, P, prm).cpu().numpy()
     scale = np.abs(Ao - (1 - theta) * np.eye(Ao.shape[0])).max()
     assert np.abs(res[ssd.FP64] - Ao).max() < 1e-9 * scale
-    assert np.abs(res[ssd.FP32C] - Ao).max() < 1e-5 * scale
+    # FP32C: the pair-sum rounding relative to the sweep's own size
+    assert np.abs(res[ssd.FP32C] - Ao).max() < 1e-5 * np.abs(Ao).max()
     ev = np.sort(np.linalg.eigvals(res[ssd.FP64]).real)
     evo = np.sort(np.linalg.eigvals(Ao).real)
     assert np.abs(ev - evo).max() < 1e-8 * max(1.0, np.abs(evo).max())
     # a block of columns equals the same columns of the whole matrix
     blk = ssd.ddm_iteration_matrix(gpu_ctx, P, prm, col0=100, ncol=7).cpu().numpy()
-    assert np.abs(blk - res[ssd.FP32C][:, 100:107]).max() < 1e-12 * scale
+    assert np.abs(blk - res[ssd.FP32C][:, 100:107]).max() < 1e-12 * np.abs(Ao).max()
     P.release()
