@@ -241,6 +241,11 @@ def oracle_leg(args, c5, c2rows, xyz5, nrm5, w5, xyz2, nrm2, w2):
     r1 = S.ddm_solve(pts1, 3.0 / 8, 1.0, 1.0, 0.0, (0.0, 0.0, 1.0), 0.75, tol=1e-9, maxit=60, outer="gmres",
                      traction="jt")
     c1_s = time.perf_counter() - t0
+    # one C2 case in full: kappa = 1, gamma = 0.1, lagged BJS, the bench's tolerances
+    t0 = time.perf_counter()
+    r2o = S.ddm_solve(pts2, 3 * H2, 1.0, 1.0, 0.1, (0.0, 0.0, 1.0), 0.5, tol=TOL_OUTER, maxit=100, outer="gmres",
+                      traction="bjs", inner_tol=TOL_INNER, restart=256)
+    c2_s = time.perf_counter() - t0
     rates = {"sphere h=1/8 (N=%d), full" % pts1["w"].size: oracle_operator_rates(pts1, 3.0 / 8),
              "sphere h=1/32 (N=%d), full" % w2.size: oracle_operator_rates(pts2, 3 * H2),
              "ellipsoid h=1/128 (N=%d), every 64th target row, scaled" % w5.size:
@@ -261,6 +266,9 @@ def oracle_leg(args, c5, c2rows, xyz5, nrm5, w5, xyz2, nrm2, w2):
                 "ddm_time_to_solution_s": {"C1 sphere h=1/8 porous-sphere benchmark (kappa=1, theta=0.75, "
                                            "interface GMRES 1e-9), run in full": c1_s,
                                            "C1_outer_its": r1["outer_its"],
+                                           "C2 sphere h=1/32 kappa=1 gamma=0.1 lagged BJS (interface GMRES 1e-8, "
+                                           "local 1e-9), run in full": c2_s,
+                                           "C2_kappa1_gamma0.1_outer_its": r2o["outer_its"],
                                            "C2 rows": "oracle_s_extrapolated in each sphere row (per-operator "
                                                       "time x the device solve's operator counts)"}}
 
