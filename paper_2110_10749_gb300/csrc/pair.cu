@@ -653,14 +653,16 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
 }
 
 // ------------------------------------------------- symmetric far block pairs
-// The double layers evaluated once per unordered pair of points in two
-// blocks of the layout that are farther apart than rho_far delta (bare
+// The four layer operators evaluated once per unordered pair of points in
+// two blocks of the layout that are farther apart than rho_far delta (bare
 // kernels, s_i = 1).  For targets a and sources b with yh = y_a - x_b, and
 // m = w n:
-//   Stokes:  A = (yh . (u_b - u_a)) / r^5,
-//            a <- A (yh . m_b) yh,   b <- A (yh . m_a) yh
-//   Laplace: B = (p_b - p_a) / r^3,
-//            a <- B (yh . m_b),      b <- B (yh . m_a)
+//   Stokes DL:  A = (yh . (u_b - u_a)) / r^5,
+//               a <- A (yh . m_b) yh,   b <- A (yh . m_a) yh
+//   Laplace DL: B = (p_b - p_a) / r^3,
+//               a <- B (yh . m_b),      b <- B (yh . m_a)
+//   single layers (kernels even in yh, densities packed with w):
+//               a <- S(yh) (w f)_b,     b <- S(yh) (w f)_a
 // (the reverse terms follow from yh -> -yh and swapping the roles), so r, its
 // powers and the density difference are shared by both directions.
 // A CTA holds 512 targets (4 per thread) of one block and walks source tiles
@@ -745,7 +747,22 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
                 const float2 ri2 = mul2(ri, ri);
                 const float2 ynb = fma2(dz, bc2(sw.z), fma2(dy, bc2(sw.y), mul2(dx, bc2(sw.x))));
                 const float2 yna = fma2(dz, tm[k][2], fma2(dy, tm[k][1], mul2(dx, tm[k][0])));
-                if (OP == OP_SDL) {
+                if (OP == OP_LSL) {
+                    // G is even in yh: a <- (w g)_b / r, b <- (w g)_a / r
+                    part[k][0] = fma2(bc2(s0.x), ri, part[k][0]);
+                    rv[0] = fma2(dt[k][0], ri, rv[0]);
+                } else if (OP == OP_SSL) {
+                    // S is even in yh: a <- f_b / r + yh (yh . f_b) / r^3 (f = w f), and so for b
+                    const float2 ri3 = mul2(ri2, ri);
+                    const float2 bb = mul2(fma2(dz, bc2(s0.z), fma2(dy, bc2(s0.y), mul2(dx, bc2(s0.x)))), ri3);
+                    const float2 ba = mul2(fma2(dz, dt[k][2], fma2(dy, dt[k][1], mul2(dx, dt[k][0]))), ri3);
+                    part[k][0] = fma2(bc2(s0.x), ri, fma2(bb, dx, part[k][0]));
+                    part[k][1] = fma2(bc2(s0.y), ri, fma2(bb, dy, part[k][1]));
+                    part[k][2] = fma2(bc2(s0.z), ri, fma2(bb, dz, part[k][2]));
+                    rv[0] = fma2(dt[k][0], ri, fma2(ba, dx, rv[0]));
+                    rv[1] = fma2(dt[k][1], ri, fma2(ba, dy, rv[1]));
+                    rv[2] = fma2(dt[k][2], ri, fma2(ba, dz, rv[2]));
+                } else if (OP == OP_SDL) {
                     const float2 ux = sub2(bc2(s0.x), dt[k][0]), uy = sub2(bc2(s0.y), dt[k][1]),
                                  uz = sub2(bc2(s0.z), dt[k][2]);
                     const float2 du = fma2(uz, dz, fma2(uy, dy, mul2(ux, dx)));
@@ -1254,7 +1271,7 @@ int item_order(ssd_ctx *ctx, const Layout &L, int slot, int tpb, int tpt, int64_
     return SSD_OK;
 }
 
-// Work lists of the symmetric plan of the FP32C double layers (see
+// Work lists of the symmetric plan of the FP32C layer operators (see
 // sym32_kernel), built once per prepared layout and rho_far delta from the
 // chunk boxes.  Blocks of 512 points: a pair of blocks whose boxes (of their
 // real points) are farther apart than rho_far delta goes to the symmetric
@@ -1424,11 +1441,12 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const size_t o_d1 = two_rec ? carve(rec * n_pad) : 0;
     const size_t o_part = carve(rsz * nslot * nc * nsplit * n_pad);
     const size_t o_wdot = carve(sizeof(double) * pack_blocks);
-    // FP32C double layers on a prepared layout: the symmetric plan when far
+    // FP32C layer operators on a prepared layout: the symmetric plan when far
     // block pairs are most of the work (FP64 accumulator instead of partials)
     const bool rows_req = pc.row_end >= 0;
     bool use_sym = false;
-    if (packed32 && (op == OP_SDL || op == OP_LDL) && !rows_req && ctx->sym && L.order_ok) {
+    if (packed32 && (op == OP_SDL || op == OP_LDL || op == OP_SSL || op == OP_LSL) && !rows_req && ctx->sym &&
+        L.order_ok) {
         SSD_TRY(sym_plan(ctx, L, make_consts<float>(pc.delta, kRhoFar32), s));
         use_sym = L.sym_use;
     }
@@ -1493,7 +1511,12 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     cudaError_t e;
     if (use_sym) {
         const float4 *d0 = reinterpret_cast<const float4 *>(base + o_d0);
-        e = op == OP_SDL ? launch_sym<OP_SDL>(L, d0, acc, s) : launch_sym<OP_LDL>(L, d0, acc, s);
+        switch (op) {
+            case OP_SDL: e = launch_sym<OP_SDL>(L, d0, acc, s); break;
+            case OP_LDL: e = launch_sym<OP_LDL>(L, d0, acc, s); break;
+            case OP_SSL: e = launch_sym<OP_SSL>(L, d0, acc, s); break;
+            default: e = launch_sym<OP_LSL>(L, d0, acc, s); break;
+        }
         if (L.sym_far) ctx->launches++;   // near items and far items: two launches
     } else if (f32 && transposed) {
         KArgs<float> ka;

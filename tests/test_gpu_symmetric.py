@@ -1,8 +1,9 @@
-"""The FP32C double layers on the symmetric plan (far block pairs evaluated
+"""The FP32C layer operators on the symmetric plan (far block pairs evaluated
 once for both directions): on the h = 1/48 sphere (N = 38310, 64% of the
-pairs in far block pairs) the whole application against the oracle element
-by element, and against the same operator with the plan switched off
-(SSD_PAIR_SYM=0 when the context is created)."""
+pairs in far block pairs) the whole application of each of the four
+operators against the oracle element by element, and against the same
+operator with the plan switched off (SSD_PAIR_SYM=0 when the context is
+created)."""
 import os
 
 import numpy as np
@@ -29,9 +30,13 @@ def test_symmetric_plan_matches_oracle_and_direct_kernel(gpu_ctx):
     P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
     outL = ssd.laplace_DL(gpu_ctx, P, d, tg, ssd.FP32C).cpu().numpy()
     outS = ssd.stokes_DL(gpu_ctx, P, d, tv, ssd.FP32C).cpu().numpy()
+    outl = ssd.laplace_SL(gpu_ctx, P, d, tg, ssd.FP32C).cpu().numpy()
+    outs = ssd.stokes_SL(gpu_ctx, P, d, 1.3, tv, ssd.FP32C).cpu().numpy()
     refL = oracle.laplace_dl(p, d, g)
     refS = oracle.stokes_dl(p, d, v)
-    for a, b in ((outL, refL), (outS, refS)):
+    refl = oracle.laplace_sl(p, d, g)
+    refs = oracle.stokes_sl(p, d, 1.3, v)
+    for a, b in ((outL, refL), (outS, refS), (outl, refl), (outs, refs)):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
         assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
     # the direct kernel (plan off) on the same points agrees to FP32C rounding
@@ -47,8 +52,10 @@ def test_symmetric_plan_matches_oracle_and_direct_kernel(gpu_ctx):
     P2 = ssd.Points.from_numpy(p).prepare(ctx2)
     dL = ssd.laplace_DL(ctx2, P2, d, tg, ssd.FP32C).cpu().numpy()
     dS = ssd.stokes_DL(ctx2, P2, d, tv, ssd.FP32C).cpu().numpy()
-    assert np.linalg.norm(dL - outL) / np.linalg.norm(refL) < 1e-6
-    assert np.linalg.norm(dS - outS) / np.linalg.norm(refS) < 1e-6
+    dl = ssd.laplace_SL(ctx2, P2, d, tg, ssd.FP32C).cpu().numpy()
+    ds = ssd.stokes_SL(ctx2, P2, d, 1.3, tv, ssd.FP32C).cpu().numpy()
+    for a, b, ref in ((dL, outL, refL), (dS, outS, refS), (dl, outl, refl), (ds, outs, refs)):
+        assert np.linalg.norm(a - b) / np.linalg.norm(ref) < 1e-6
     # the plan's two launches are counted under the double-layer classes
     gpu_ctx.reset_stats()
     gpu_ctx.set_timing(True)
