@@ -506,6 +506,62 @@ int successive(ssd_ctx *ctx, cudaStream_t s, int64_t n, const std::function<int(
 
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
+// Mixed-precision iterative refinement of one local system A x = b
+// (Wilkinson's scheme, as in Moler 1967): the residual r = b - A x with the
+// FP64 operator `A_hi`, the correction from A_lo e = r by GMRES with the
+// FP32C operator `A_lo`, x += e, until ||r|| <= tol ||b||.  The correction
+// only has to take the residual down by tol ||b|| / ||r||: the operators
+// differ by the FP32 pair-term rounding (about 1e-7 relative), so from a start
+// that is already FP32C-accurate one correction and one check suffice, i.e.
+// two FP64 applications instead of one per Krylov step.  res->iters counts
+// the FP32C correction steps; res->relres is the last FP64 residual.
+int ir_solve(ssd_ctx *ctx, cudaStream_t s, int64_t n, const MatVec &A_hi, const MatVec &A_lo, const double *b,
+             double *x, double tol, int restart, int maxit, bool warm, GmresResult *res, int max_ref = 4) {
+    Buf r, e, scal;
+    SSD_TRY(r.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(e.alloc(ctx, sizeof(double) * n));
+    SSD_TRY(scal.alloc(ctx, sizeof(double) * 2));
+    Dots dots;
+    SSD_TRY(dots.init(ctx, s, 1));
+    const unsigned gb = grid_for(n);
+    SSD_TRY(dots.multi(b, 0, 1, b, n, scal.d()));
+    double h[1];
+    SSD_TRY(read_scalars(ctx, scal.d(), 1, h, s));
+    const double bnorm = sqrt(h[0]);
+    if (!isfinite(bnorm)) return set_error(ctx, SSD_ENUMERIC, "non-finite right-hand side");
+    res->iters = 0;
+    res->relres = 0.0;
+    if (!warm || bnorm == 0.0) SSD_TRY(cuda_check(ctx, cudaMemsetAsync(x, 0, sizeof(double) * n, s), "memset"));
+    if (bnorm == 0.0) return SSD_OK;
+    for (int k = 0;; ++k) {
+        if (k == 0 && !warm) {
+            SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(r.d(), b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s),
+                               "copy"));
+        } else {
+            SSD_TRY(A_hi(x, r.d()));
+            axpby_kernel<<<gb, 256, 0, s>>>(n, 1.0, b, -1.0, r.d());   // r = b - A x
+            ctx->launches++;
+        }
+        SSD_TRY(dots.multi(r.d(), 0, 1, r.d(), n, scal.d()));
+        SSD_TRY(read_scalars(ctx, scal.d(), 1, h, s));
+        const double rel = sqrt(h[0]) / bnorm;
+        res->relres = rel;
+        if (!isfinite(rel)) return set_error(ctx, SSD_ENUMERIC, "non-finite refinement residual");
+        if (rel <= tol) return SSD_OK;
+        if (k >= max_ref || res->iters >= maxit)
+            return set_error(ctx, SSD_ENOTCONV, "local refinement reached its iteration limit");
+        GmresResult ge;
+        const double tc = fmax(0.5 * tol / rel, 1e-6);
+        const int st = gmres(ctx, s, n, A_lo, r.d(), e.d(), tc, restart, maxit - res->iters, false, &ge);
+        if (st != SSD_OK && st != SSD_ENOTCONV) return st;
+        res->iters += ge.iters;
+        axpby_kernel<<<gb, 256, 0, s>>>(n, 1.0, e.d(), 1.0, x);
+        ctx->launches++;
+        SSD_TRY(launch_check(ctx, "refinement update"));
+    }
+}
+
+
 int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
     if (!kr) return set_error(ctx, SSD_EINVAL, "krylov settings are NULL");
     if (!(kr->tol > 0.0) || !isfinite(kr->tol)) return set_error(ctx, SSD_EINVAL, "tolerance must be positive");
@@ -519,7 +575,7 @@ int check_krylov(ssd_ctx *ctx, const ssd_krylov *kr) {
 // ------------------------------------------------------------- local solves
 int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu, double kappa,
                      const double *q, double *p, const ssd_krylov &kr, GmresResult *res, cudaStream_t s,
-                     bool gauge = true, bool warm = false) {
+                     bool gauge = true, bool warm = false, bool mixed = false) {
     const int64_t n = pts->n;
     Buf b, scal;
     SSD_TRY(b.alloc(ctx, sizeof(double) * n));
@@ -548,13 +604,18 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
         st = successive(ctx, s, n, step, p, kr.tol, kr.maxit, res, warm);
     } else {
         // -D^L p + (w . p)/sum(w): nonsingular, same solution for consistent b
-        auto A = [&](const double *x, double *y) -> int {
-            PairCall a;
-            a.op = OP_LDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.a_op = -1.0;
-            a.rank1_weight_mean = true; a.out = y;
-            return pair_apply(ctx, L, a, s);
+        auto Ap = [&](int prec) {
+            return [&, prec](const double *x, double *y) -> int {
+                PairCall a;
+                a.op = OP_LDL; a.prec = prec; a.delta = delta; a.dens0 = x; a.a_op = -1.0;
+                a.rank1_weight_mean = true; a.out = y;
+                return pair_apply(ctx, L, a, s);
+            };
         };
-        st = gmres(ctx, s, n, A, b.d(), p, kr.tol, kr.restart, kr.maxit, warm, res);
+        if (mixed && kr.prec == SSD_FP64)
+            st = ir_solve(ctx, s, n, Ap(SSD_FP64), Ap(SSD_FP32C), b.d(), p, kr.tol, kr.restart, kr.maxit, warm, res);
+        else
+            st = gmres(ctx, s, n, Ap(kr.prec), b.d(), p, kr.tol, kr.restart, kr.maxit, warm, res);
     }
     if (st != SSD_OK && st != SSD_ENOTCONV) return st;
     if (!gauge) return st;
@@ -570,7 +631,7 @@ int darcy_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doubl
 
 int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
                       const double *f, const double uinf[3], double *u, const ssd_krylov &kr, GmresResult *res,
-                      cudaStream_t s, bool warm = false) {
+                      cudaStream_t s, bool warm = false, bool mixed = false) {
     const int64_t n = pts->n;
     Buf b;
     SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
@@ -592,14 +653,18 @@ int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doub
         return successive(ctx, s, 3 * n, step, u, kr.tol, kr.maxit, res, warm);
     }
     // (I - D^S) u  [+ n (w . (u.n))/sum(w) when deflating]
-    auto A = [&](const double *x, double *y) -> int {
-        PairCall a;
-        a.op = OP_SDL; a.prec = kr.prec; a.delta = delta; a.dens0 = x; a.xin = x; a.a_id = 1.0; a.a_op = -1.0;
-        a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
-        a.out = y;
-        return pair_apply(ctx, L, a, s);
+    auto Ap = [&](int prec) {
+        return [&, prec](const double *x, double *y) -> int {
+            PairCall a;
+            a.op = OP_SDL; a.prec = prec; a.delta = delta; a.dens0 = x; a.xin = x; a.a_id = 1.0; a.a_op = -1.0;
+            a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
+            a.out = y;
+            return pair_apply(ctx, L, a, s);
+        };
     };
-    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
+    if (mixed && kr.prec == SSD_FP64)
+        return ir_solve(ctx, s, 3 * n, Ap(SSD_FP64), Ap(SSD_FP32C), b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
+    return gmres(ctx, s, 3 * n, Ap(kr.prec), b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
 }
 
 // Stokes step with the BJS slip at its own velocity: with f = -p n + c P u
@@ -608,7 +673,7 @@ int stokes_solve_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, doub
 // the matvec is one fused single+double layer pass.
 int stokes_solve_bjs_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, double delta, double mu,
                           const double *p, const double uinf[3], double c, double *u, const ssd_krylov &kr,
-                          GmresResult *res, cudaStream_t s, bool warm = false) {
+                          GmresResult *res, cudaStream_t s, bool warm = false, bool mixed = false) {
     const int64_t n = pts->n;
     Buf b, tmp;
     SSD_TRY(b.alloc(ctx, sizeof(double) * 3 * n));
@@ -619,16 +684,20 @@ int stokes_solve_bjs_impl(ssd_ctx *ctx, const ssd_points *pts, const Layout &L, 
     pc.op = OP_SSL; pc.prec = kr.prec; pc.delta = delta; pc.mu = mu; pc.dens0 = tmp.d(); pc.a_op = 1.0;
     pc.add[0] = uinf[0]; pc.add[1] = uinf[1]; pc.add[2] = uinf[2]; pc.out = b.d();
     SSD_TRY(pair_apply(ctx, L, pc, s));
-    auto A = [&](const double *x, double *y) -> int {
-        tangential_kernel<<<grid_for(n), 256, 0, s>>>(n, x, pts->nrm, tmp.d());
-        ctx->launches++;
-        PairCall a;
-        a.op = OP_SSLDL; a.prec = kr.prec; a.delta = delta; a.mu = mu; a.dens0 = x; a.dens1 = tmp.d();
-        a.alpha = c; a.beta = -1.0; a.xin = x; a.a_id = 1.0; a.a_op = 1.0; a.out = y;
-        a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
-        return pair_apply(ctx, L, a, s);
+    auto Ap = [&](int prec) {
+        return [&, prec](const double *x, double *y) -> int {
+            tangential_kernel<<<grid_for(n), 256, 0, s>>>(n, x, pts->nrm, tmp.d());
+            ctx->launches++;
+            PairCall a;
+            a.op = OP_SSLDL; a.prec = prec; a.delta = delta; a.mu = mu; a.dens0 = x; a.dens1 = tmp.d();
+            a.alpha = c; a.beta = -1.0; a.xin = x; a.a_id = 1.0; a.a_op = 1.0; a.out = y;
+            a.rank1_nrm = kr.deflate ? pts->nrm : nullptr;
+            return pair_apply(ctx, L, a, s);
+        };
     };
-    return gmres(ctx, s, 3 * n, A, b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
+    if (mixed && kr.prec == SSD_FP64)
+        return ir_solve(ctx, s, 3 * n, Ap(SSD_FP64), Ap(SSD_FP32C), b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
+    return gmres(ctx, s, 3 * n, Ap(kr.prec), b.d(), u, kr.tol, kr.restart, kr.maxit, warm, res);
 }
 
 // ------------------------------------------------------------------ D-N solve
@@ -643,6 +712,7 @@ struct Ddm {
     std::vector<int> inner;   // (darcy, stokes) per sweep
     int nonconv = 0;
     bool start_from_outputs = false;   // local solves start from the contents of p and u
+    bool mixed = false;                // FP64 local solves by refinement with FP32C corrections (ir_solve)
 
     // one sweep: (q, uprev) -> (qn, u); p and f are left in pbuf and f
     int sweep(const double *q, const double *uprev, double *qn, double *u, double *p) {
@@ -654,12 +724,13 @@ struct Ddm {
         if (warm && !start_from_outputs && u != uprev)
             SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(u, uprev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s),
                                "warm start copy"));
-        int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s, true, warm);
+        int st = darcy_solve_impl(ctx, pts, *L, P.delta, P.mu, P.kappa, q, p, P.inner, &rd, s, true, warm, mixed);
         if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
         SSD_TRY(st);
         if (P.traction_mode == SSD_TRACTION_BJS && P.bjs_implicit) {
             const double coef = P.bjs_sign * P.gamma / sqrt(P.kappa);
-            st = stokes_solve_bjs_impl(ctx, pts, *L, P.delta, P.mu, p, P.uinf, coef, u, P.inner, &rs, s, warm);
+            st = stokes_solve_bjs_impl(ctx, pts, *L, P.delta, P.mu, p, P.uinf, coef, u, P.inner, &rs, s, warm,
+                                       mixed);
             if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
             SSD_TRY(st);
             traction_bjs_kernel<<<grid_for(n), 256, 0, s>>>(n, p, u, pts->nrm, coef, f.d());
@@ -682,7 +753,7 @@ struct Ddm {
         }
         ctx->launches++;
         SSD_TRY(launch_check(ctx, "traction"));
-        st = stokes_solve_impl(ctx, pts, *L, P.delta, P.mu, f.d(), P.uinf, u, P.inner, &rs, s, warm);
+        st = stokes_solve_impl(ctx, pts, *L, P.delta, P.mu, f.d(), P.uinf, u, P.inner, &rs, s, warm, mixed);
         if (st == SSD_ENOTCONV) { nonconv++; st = SSD_OK; }
         SSD_TRY(st);
         q_update_kernel<<<grid_for(n), 256, 0, s>>>(n, P.theta, q, u, pts->nrm, qn);
@@ -813,7 +884,7 @@ int ddm_impl(ssd_ctx *ctx, const ssd_points *pts, const ssd_ddm_params *prm, dou
             // (I - G) z = c, from one plain-FP64 sweep; D (I - G) e = D r is
             // solved with the FP32C sweeps and z += e
             D64.ctx = ctx; D64.pts = pts; D64.L = lref.L; D64.P = *prm; D64.P.inner.prec = SSD_FP64;
-            D64.P.outer_gmres = 1; D64.s = s; D64.n = n; D64.start_from_outputs = true;
+            D64.P.outer_gmres = 1; D64.s = s; D64.n = n; D64.start_from_outputs = true; D64.mixed = true;
             SSD_TRY(D64.f.alloc(ctx, sizeof(double) * 3 * n));
             Buf rb, eb;
             SSD_TRY(rb.alloc(ctx, sizeof(double) * 4 * n));
