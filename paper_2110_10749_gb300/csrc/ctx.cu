@@ -487,7 +487,8 @@ void release_layout(ssd_ctx *ctx, Layout *L) {
     if (L->block) dev_free(ctx, L->block);
     for (int k = 0; k < 2; ++k)
         if (L->order32[k]) dev_free(ctx, L->order32[k]);
-    if (L->sym_block) dev_free(ctx, L->sym_block);
+    for (auto &pl : L->sym)
+        if (pl.block) dev_free(ctx, pl.block);
     *L = Layout();
 }
 

@@ -39,6 +39,17 @@ inline int op_components(int op) {
 
 struct alignas(16) d4 { double x, y, z, w; };
 
+// Plan that evaluates the far block pairs of a layout once for both
+// directions, cached for the last rho_far delta it was built for: near items
+// (generic or packed pair kernel in items mode) and far items (symmetric
+// kernel) in one device block.
+struct SymPlan {
+    void *block = nullptr;
+    int64_t near = 0, far = 0;
+    double rfar2 = -1.0;
+    bool use = false;
+};
+
 // Device layout of a point set: sorted copies used by the pair kernels.
 struct Layout {
     int64_t n = 0, n_pad = 0;
@@ -57,14 +68,10 @@ struct Layout {
     int2 *order32[2] = {nullptr, nullptr};
     int64_t order_nit[2] = {0, 0}, order_chunk[2] = {0, 0};
     float order_rfar2[2] = {-1.f, -1.f};
-    // plan of the FP32C double layers that evaluates far block pairs once for
-    // both directions (prepared layouts only), cached for the last
-    // rho_far delta it was built for: near items (pair32 items) and far items
-    // (symmetric kernel) in one device block
-    void *sym_block = nullptr;
-    int64_t sym_near = 0, sym_far = 0;
-    float sym_rfar2 = -1.f;
-    bool sym_use = false;
+    // plans of the layer operators that evaluate far block pairs once for
+    // both directions (prepared layouts only), one per precision:
+    // [0] FP32C, [1] FP64
+    SymPlan sym[2];
 };
 
 struct TimedLaunch {

@@ -32,6 +32,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kRhoSeries = 0.5;   // series branch below this rho (both precisions)
 constexpr double kRhoFar32 = 5.5;    // 1 - s_i(rho) < 2^-25 beyond this (FP32)
 constexpr double kRhoFar64 = 8.0;    // 1 - s_i(rho) < 1e-21 beyond this (FP64)
+// symmetric plans: blocks of 512 layout points (the FP32C CTA's target span,
+// a divisor of n_pad), far items of at most kSymTiles source tiles
+constexpr int kSymBlock = kTPB32 * kTPT32;
+constexpr int kSymTiles = 8;
 
 template <int OP> struct OpInfo;
 template <> struct OpInfo<OP_LSL>   { enum { NC = 1, WN = 0, D1 = 0, SL = 1, DL = 0 }; };
@@ -59,7 +63,7 @@ template <> struct Prec<float> {
 };
 template <> struct Prec<double> {
     typedef d4 V4;
-    static __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double erf_(double x) { return erf(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ double ser(int i, double t) {
@@ -102,6 +106,8 @@ template <typename R> struct KArgs {
     int64_t part_stride;       // partial values per right-hand side
     const int2 *order = nullptr;   // single-surface launch order: blockIdx.x -> (target tile, split)
     int64_t tile0 = 0;             // single-surface launch without order: first target tile
+    double *acc = nullptr;         // items of one surface: add each sum to acc[c][i] atomically
+                                   // instead of writing per-split partials
 };
 
 // Smoothed radial factors k1 = s1/r, k2 = s2/r^3, k3 = s3/r^3, k4 = s4/r^5
@@ -334,6 +340,18 @@ __global__ void __launch_bounds__(TPB) pair_kernel(const KArgs<R> a) {
     }
     // partial layout: [split][comp][slot][n_pad], slot = hi (and lo for FP32)
     constexpr int NS = sizeof(Acc<R>) / sizeof(R);
+    if (a.acc) {
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            const int64_t i = tbase + threadIdx.x + t * TPB;
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                const R *v = reinterpret_cast<const R *>(&acc[t][q]);
+                atomicAdd(a.acc + q * a.n_pad + i, NS == 2 ? (double)v[0] + (double)v[1] : (double)v[0]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         const int64_t i = tbase + threadIdx.x + t * TPB;
@@ -817,6 +835,137 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
     }
 }
 
+// FP64 counterpart of sym32_kernel on the same block plan: a CTA of 128
+// threads holds the 512 targets of one block, 4 per thread (threadIdx.x +
+// 128 t), and walks the source tiles of its item with the same lane-rotated
+// source order and per-warp reverse sums.  Sources are staged as separate
+// coordinate arrays (one double per bank pair per lane).  The per-pair work
+// shared by both directions (the displacement, r, its powers, the density
+// difference) is done once.
+struct Sym64Args {
+    const d4 *pos, *wn, *d0;
+    const SymItem *items;
+    int64_t n_pad;
+    double *acc;               // [NC][n_pad]
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kTPB64) sym64_kernel(const Sym64Args a) {
+    constexpr int NC = OpInfo<OP>::NC;
+    constexpr int DL = OpInfo<OP>::DL;
+    constexpr int TT = kSymBlock / kTPB64;
+    constexpr int NW = kTPB64 / 32;
+    static_assert(kTile == kTPB64, "one staged source per thread");
+    __shared__ double sm_p[3][kTile];
+    __shared__ double sm_m[DL ? 3 : 1][kTile];
+    __shared__ double sm_d[NC][kTile];
+    __shared__ double sm_rev[NC][NW][kTile];
+    const SymItem it = a.items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double y[TT][3], dt[TT][NC], tm[TT][DL ? 3 : 1], tacc[TT][NC];
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+        const int64_t i = it.tb + threadIdx.x + t * kTPB64;
+        const d4 p = a.pos[i], d = a.d0[i];
+        y[t][0] = p.x; y[t][1] = p.y; y[t][2] = p.z;
+        dt[t][0] = d.x;
+        if constexpr (NC == 3) { dt[t][1] = d.y; dt[t][2] = d.z; }
+        if constexpr (DL) {
+            const d4 m = a.wn[i];
+            tm[t][0] = m.x; tm[t][1] = m.y; tm[t][2] = m.z;
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) tacc[t][q] = 0.0;
+    }
+    for (int64_t tile = it.s0; tile < it.s1; tile += kTile) {
+        __syncthreads();
+        {
+            const int64_t j = tile + threadIdx.x;
+            const d4 p = a.pos[j], d = a.d0[j];
+            sm_p[0][threadIdx.x] = p.x; sm_p[1][threadIdx.x] = p.y; sm_p[2][threadIdx.x] = p.z;
+            sm_d[0][threadIdx.x] = d.x;
+            if constexpr (NC == 3) { sm_d[1][threadIdx.x] = d.y; sm_d[2][threadIdx.x] = d.z; }
+            if constexpr (DL) {
+                const d4 m = a.wn[j];
+                sm_m[0][threadIdx.x] = m.x; sm_m[1][threadIdx.x] = m.y; sm_m[2][threadIdx.x] = m.z;
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sm_rev[q][w][threadIdx.x] = 0.0;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int st = 0; st < kTile; ++st) {
+            const int j = (lane + st) & (kTile - 1);
+            const double sx = sm_p[0][j], sy = sm_p[1][j], sz = sm_p[2][j];
+            double s0[NC], sm[3] = {0.0, 0.0, 0.0}, rv[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) { s0[q] = sm_d[q][j]; rv[q] = 0.0; }
+            if constexpr (DL) { sm[0] = sm_m[0][j]; sm[1] = sm_m[1][j]; sm[2] = sm_m[2][j]; }
+#pragma unroll
+            for (int t = 0; t < TT; ++t) {
+                const double dx = y[t][0] - sx, dy = y[t][1] - sy, dz = y[t][2] - sz;
+                const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                const double ri = rsqrt(r2);
+                if constexpr (OP == OP_LSL) {
+                    tacc[t][0] = fma(s0[0], ri, tacc[t][0]);
+                    rv[0] = fma(dt[t][0], ri, rv[0]);
+                } else if constexpr (OP == OP_SSL) {
+                    const double ri3 = ri * ri * ri;
+                    const double bb = fma(dz, s0[2], fma(dy, s0[1], dx * s0[0])) * ri3;
+                    const double ba = fma(dz, dt[t][2], fma(dy, dt[t][1], dx * dt[t][0])) * ri3;
+                    tacc[t][0] = fma(s0[0], ri, fma(bb, dx, tacc[t][0]));
+                    tacc[t][1] = fma(s0[1], ri, fma(bb, dy, tacc[t][1]));
+                    tacc[t][2] = fma(s0[2], ri, fma(bb, dz, tacc[t][2]));
+                    rv[0] = fma(dt[t][0], ri, fma(ba, dx, rv[0]));
+                    rv[1] = fma(dt[t][1], ri, fma(ba, dy, rv[1]));
+                    rv[2] = fma(dt[t][2], ri, fma(ba, dz, rv[2]));
+                } else {
+                    const double ynb = fma(dz, sm[2], fma(dy, sm[1], dx * sm[0]));
+                    const double yna = fma(dz, tm[t][2], fma(dy, tm[t][1], dx * tm[t][0]));
+                    const double ri2 = ri * ri;
+                    if constexpr (OP == OP_LDL) {
+                        // B = (p_b - p_a) / r^3: a <- B (yh . m_b), b <- B (yh . m_a)
+                        const double B = (s0[0] - dt[t][0]) * (ri2 * ri);
+                        tacc[t][0] = fma(B, ynb, tacc[t][0]);
+                        rv[0] = fma(B, yna, rv[0]);
+                    } else {
+                        // A = (yh . (u_b - u_a)) / r^5: a <- A (yh . m_b) yh, b <- A (yh . m_a) yh
+                        const double du = fma(dz, s0[2] - dt[t][2], fma(dy, s0[1] - dt[t][1], dx * (s0[0] - dt[t][0])));
+                        const double A = du * (ri2 * ri2 * ri);
+                        const double ab = A * ynb, aa = A * yna;
+                        tacc[t][0] = fma(ab, dx, tacc[t][0]);
+                        tacc[t][1] = fma(ab, dy, tacc[t][1]);
+                        tacc[t][2] = fma(ab, dz, tacc[t][2]);
+                        rv[0] = fma(aa, dx, rv[0]);
+                        rv[1] = fma(aa, dy, rv[1]);
+                        rv[2] = fma(aa, dz, rv[2]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q) sm_rev[q][warp][j] += rv[q];
+        }
+        // reverse: the four warps' sums of source tile + threadIdx.x
+        __syncthreads();
+        const int64_t jb = tile + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            double r = sm_rev[q][0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) r += sm_rev[q][w][threadIdx.x];
+            atomicAdd(a.acc + q * a.n_pad + jb, r);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+        const int64_t i = it.tb + threadIdx.x + t * kTPB64;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) atomicAdd(a.acc + q * a.n_pad + i, tacc[t][q]);
+    }
+}
+
 // ------------------------------------------------------------------- packing
 // Densities in the layout's order, scaled for the kernel; padding slots zero.
 struct PackArgs {
@@ -1271,23 +1420,27 @@ int item_order(ssd_ctx *ctx, const Layout &L, int slot, int tpb, int tpt, int64_
     return SSD_OK;
 }
 
-// Work lists of the symmetric plan of the FP32C layer operators (see
-// sym32_kernel), built once per prepared layout and rho_far delta from the
-// chunk boxes.  Blocks of 512 points: a pair of blocks whose boxes (of their
-// real points) are farther apart than rho_far delta goes to the symmetric
-// kernel, in items of the target block against at most kSymTiles source
-// tiles; the diagonal blocks and the near block pairs (both directions) are
-// items of pair32_kernel.  The plan is used when far pairs are at least half
-// of all pairs.
-constexpr int kSymBlock = kTPB32 * kTPT32;
-constexpr int kSymTiles = 8;
-
-int sym_plan(ssd_ctx *ctx, const Layout &L, const Consts<float> &c, cudaStream_t s) {
+// Work lists of the symmetric plan of the layer operators (see sym32_kernel
+// and sym64_kernel), built once per prepared layout, precision and
+// rho_far delta from the chunk boxes.  Blocks of 512 points: a pair of blocks
+// whose boxes (of their real points) are farther apart than rho_far delta
+// goes to the symmetric kernel, in items of the target block against at most
+// kSymTiles source tiles; the diagonal blocks and the near block pairs (both
+// directions) are items of the pair kernel of the precision (slot 0:
+// pair32_kernel, one item of 512 targets; slot 1: the generic FP64 kernel,
+// four items of 128 targets).  The plan is used when far pairs are at least
+// half of all pairs.  The device block holds the surface descriptor, the
+// kernel constants (`cbytes` bytes at `consts`), the near and the far items.
+int sym_plan(ssd_ctx *ctx, const Layout &L, int slot, double rfar2, const void *consts, size_t cbytes,
+             cudaStream_t s) {
     Layout &M = const_cast<Layout &>(L);
-    if (M.sym_rfar2 == c.rfar2) return SSD_OK;
-    if (M.sym_block) { dev_free(ctx, M.sym_block); M.sym_block = nullptr; }
-    M.sym_use = false;
-    M.sym_near = M.sym_far = 0;
+    SymPlan &pl = M.sym[slot];
+    if (pl.rfar2 == rfar2) return SSD_OK;
+    if (pl.block) { dev_free(ctx, pl.block); pl.block = nullptr; }
+    pl.use = false;
+    pl.near = pl.far = 0;
+    const int nsub = slot == 0 ? 1 : kSymBlock / (kTPB64 * kTPT64);   // near items per block pair
+    const int sub = kSymBlock / nsub;
     const int64_t n = L.n, n_pad = L.n_pad, nb = n_pad / kSymBlock, nch = n_pad / kChunk;
     std::vector<float4> cb(2 * nch);
     SSD_TRY(cuda_check(ctx, cudaMemcpyAsync(cb.data(), L.cbox, sizeof(float4) * 2 * nch, cudaMemcpyDeviceToHost, s),
@@ -1311,21 +1464,23 @@ int sym_plan(ssd_ctx *ctx, const Layout &L, const Consts<float> &c, cudaStream_t
             const double g = fmax(0.0, fmax((double)blo[3 * k + q] - bhi[3 * i + q], (double)blo[3 * i + q] - bhi[3 * k + q]));
             g2 += g * g;
         }
-        return g2 >= (double)c.rfar2;
+        return g2 >= rfar2;
     };
     std::vector<BItem> near;
     std::vector<SymItem> far;
     int64_t far_blocks = 0;
+    auto near_item = [&](int64_t ti, int64_t si) {   // targets of block ti against sources of block si
+        for (int q = 0; q < nsub; ++q)
+            near.push_back(BItem{(int32_t)(ti * kSymBlock + q * sub), (int32_t)(si * kSymBlock),
+                                 (int32_t)((si + 1) * kSymBlock), 0, 0, 0, 0, 0});
+    };
     for (int64_t i = 0; i < nb; ++i) {
-        near.push_back(BItem{(int32_t)(i * kSymBlock), (int32_t)(i * kSymBlock), (int32_t)((i + 1) * kSymBlock),
-                             0, 0, 0, 0, 0});
+        near_item(i, i);
         int64_t k = i + 1;
         while (k < nb) {
             if (!far_pair(i, k)) {
-                near.push_back(BItem{(int32_t)(i * kSymBlock), (int32_t)(k * kSymBlock),
-                                     (int32_t)((k + 1) * kSymBlock), 0, 0, 0, 0, 0});
-                near.push_back(BItem{(int32_t)(k * kSymBlock), (int32_t)(i * kSymBlock),
-                                     (int32_t)((i + 1) * kSymBlock), 0, 0, 0, 0, 0});
+                near_item(i, k);
+                near_item(k, i);
                 ++k;
                 continue;
             }
@@ -1340,12 +1495,12 @@ int sym_plan(ssd_ctx *ctx, const Layout &L, const Consts<float> &c, cudaStream_t
             k = k1;
         }
     }
-    M.sym_rfar2 = c.rfar2;
+    pl.rfar2 = rfar2;
     // far pairs (both directions) against all ordered pairs
     if (2.0 * (double)far_blocks < 0.5 * (double)nb * (double)nb) return SSD_OK;
     size_t off = 0;
     auto carve = [&](size_t b) { size_t o = off; off += (b + 255) & ~size_t(255); return o; };
-    const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(sizeof(Consts<float>));
+    const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(cbytes);
     const size_t o_near = carve(sizeof(BItem) * near.size()), o_far = carve(sizeof(SymItem) * far.size());
     void *blk = nullptr;
     SSD_TRY(dev_alloc(ctx, off, &blk));
@@ -1353,27 +1508,28 @@ int sym_plan(ssd_ctx *ctx, const Layout &L, const Consts<float> &c, cudaStream_t
     const BSurf sf{0, n_pad, n, 0, 1, 0, 0, 0};
     std::vector<char> host(off);
     memcpy(host.data() + o_surf, &sf, sizeof(sf));
-    memcpy(host.data() + o_c, &c, sizeof(c));
+    memcpy(host.data() + o_c, consts, cbytes);
     memcpy(host.data() + o_near, near.data(), sizeof(BItem) * near.size());
     memcpy(host.data() + o_far, far.data(), sizeof(SymItem) * far.size());
     const int st = cuda_check(ctx, cudaMemcpyAsync(b, host.data(), off, cudaMemcpyHostToDevice, s), "plan copy");
     if (st == SSD_OK) SSD_TRY(cuda_check(ctx, cudaStreamSynchronize(s), "plan sync"));
     if (st != SSD_OK) { dev_free(ctx, blk); return st; }
-    M.sym_block = blk;
-    M.sym_near = (int64_t)near.size();
-    M.sym_far = (int64_t)far.size();
-    M.sym_use = true;
+    pl.block = blk;
+    pl.near = (int64_t)near.size();
+    pl.far = (int64_t)far.size();
+    pl.use = true;
     return SSD_OK;
 }
 
 template <int OP>
 cudaError_t launch_sym(const Layout &L, const float4 *d0, double *acc, cudaStream_t s) {
-    char *b = static_cast<char *>(L.sym_block);
+    const SymPlan &pl = L.sym[0];
+    char *b = static_cast<char *>(pl.block);
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
     const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(sizeof(Consts<float>));
-    const size_t o_near = carve(sizeof(BItem) * L.sym_near);
-    const size_t o_far = carve(sizeof(SymItem) * L.sym_far);
+    const size_t o_near = carve(sizeof(BItem) * pl.near);
+    const size_t o_far = carve(sizeof(SymItem) * pl.far);
     K32Args ka;
     ka.pos = L.pos32; ka.wn = L.wn32; ka.cbox = L.cbox; ka.d0 = d0; ka.d1 = d0;
     ka.n = L.n; ka.n_pad = L.n_pad; ka.chunk = kSymBlock;
@@ -1383,14 +1539,43 @@ cudaError_t launch_sym(const Layout &L, const float4 *d0, double *acc, cudaStrea
     ka.consts = reinterpret_cast<const Consts<float> *>(b + o_c);
     ka.rec_stride = 0; ka.part_stride = 0;
     ka.acc = acc;
-    pair32_kernel<OP><<<dim3((unsigned)L.sym_near, 1), kTPB32, 0, s>>>(ka);
+    pair32_kernel<OP><<<dim3((unsigned)pl.near, 1), kTPB32, 0, s>>>(ka);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || L.sym_far == 0) return e;
+    if (e != cudaSuccess || pl.far == 0) return e;
     SymArgs sa;
     sa.pos = L.pos32; sa.wn = L.wn32; sa.d0 = d0;
     sa.items = reinterpret_cast<const SymItem *>(b + o_far);
     sa.n_pad = L.n_pad; sa.acc = acc;
-    sym32_kernel<OP><<<(unsigned)L.sym_far, kTPB32, 0, s>>>(sa);
+    sym32_kernel<OP><<<(unsigned)pl.far, kTPB32, 0, s>>>(sa);
+    return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t launch_sym64(const Layout &L, const d4 *d0, double *acc, cudaStream_t s) {
+    const SymPlan &pl = L.sym[1];
+    char *b = static_cast<char *>(pl.block);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    const size_t o_surf = carve(sizeof(BSurf)), o_c = carve(sizeof(Consts<double>));
+    const size_t o_near = carve(sizeof(BItem) * pl.near);
+    const size_t o_far = carve(sizeof(SymItem) * pl.far);
+    KArgs<double> ka;
+    ka.pos = L.pos64; ka.wn = L.wn64; ka.d0 = d0; ka.d1 = d0;
+    ka.n_pad = L.n_pad; ka.chunk = kSymBlock;
+    ka.part = nullptr;
+    ka.items = reinterpret_cast<const BItem *>(b + o_near);
+    ka.surfs = reinterpret_cast<const BSurf *>(b + o_surf);
+    ka.consts = reinterpret_cast<const Consts<double> *>(b + o_c);
+    ka.rec_stride = 0; ka.part_stride = 0;
+    ka.acc = acc;
+    pair_kernel<double, OP, kTPB64, kTPT64><<<dim3((unsigned)pl.near, 1), kTPB64, 0, s>>>(ka);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || pl.far == 0) return e;
+    Sym64Args sa;
+    sa.pos = L.pos64; sa.wn = L.wn64; sa.d0 = d0;
+    sa.items = reinterpret_cast<const SymItem *>(b + o_far);
+    sa.n_pad = L.n_pad; sa.acc = acc;
+    sym64_kernel<OP><<<(unsigned)pl.far, kTPB64, 0, s>>>(sa);
     return cudaGetLastError();
 }
 
@@ -1441,14 +1626,21 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     const size_t o_d1 = two_rec ? carve(rec * n_pad) : 0;
     const size_t o_part = carve(rsz * nslot * nc * nsplit * n_pad);
     const size_t o_wdot = carve(sizeof(double) * pack_blocks);
-    // FP32C layer operators on a prepared layout: the symmetric plan when far
-    // block pairs are most of the work (FP64 accumulator instead of partials)
+    // layer operators on a prepared layout: the symmetric plan of the
+    // precision when far block pairs are most of the work (FP64 accumulator
+    // instead of partials)
     const bool rows_req = pc.row_end >= 0;
     bool use_sym = false;
-    if (packed32 && (op == OP_SDL || op == OP_LDL || op == OP_SSL || op == OP_LSL) && !rows_req && ctx->sym &&
+    if (!transposed && (op == OP_SDL || op == OP_LDL || op == OP_SSL || op == OP_LSL) && !rows_req && ctx->sym &&
         L.order_ok) {
-        SSD_TRY(sym_plan(ctx, L, make_consts<float>(pc.delta, kRhoFar32), s));
-        use_sym = L.sym_use;
+        if (f32) {
+            const Consts<float> c = make_consts<float>(pc.delta, kRhoFar32);
+            SSD_TRY(sym_plan(ctx, L, 0, c.rfar2, &c, sizeof(c), s));
+        } else {
+            const Consts<double> c = make_consts<double>(pc.delta, kRhoFar64);
+            SSD_TRY(sym_plan(ctx, L, 1, c.rfar2, &c, sizeof(c), s));
+        }
+        use_sym = L.sym[f32 ? 0 : 1].use;
     }
     const size_t o_acc = use_sym ? carve(sizeof(double) * nc * n_pad) : 0;
     void *ws = nullptr;
@@ -1509,7 +1701,7 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
     SSD_TRY(timed_begin(ctx, s, &ev));
     dim3 grid((unsigned)(tile1 - tile0), (unsigned)nsplit);
     cudaError_t e;
-    if (use_sym) {
+    if (use_sym && f32) {
         const float4 *d0 = reinterpret_cast<const float4 *>(base + o_d0);
         switch (op) {
             case OP_SDL: e = launch_sym<OP_SDL>(L, d0, acc, s); break;
@@ -1517,7 +1709,16 @@ int pair_apply(ssd_ctx *ctx, const Layout &L, const PairCall &pc, cudaStream_t s
             case OP_SSL: e = launch_sym<OP_SSL>(L, d0, acc, s); break;
             default: e = launch_sym<OP_LSL>(L, d0, acc, s); break;
         }
-        if (L.sym_far) ctx->launches++;   // near items and far items: two launches
+        if (L.sym[0].far) ctx->launches++;   // near items and far items: two launches
+    } else if (use_sym) {
+        const d4 *d0 = reinterpret_cast<const d4 *>(base + o_d0);
+        switch (op) {
+            case OP_SDL: e = launch_sym64<OP_SDL>(L, d0, acc, s); break;
+            case OP_LDL: e = launch_sym64<OP_LDL>(L, d0, acc, s); break;
+            case OP_SSL: e = launch_sym64<OP_SSL>(L, d0, acc, s); break;
+            default: e = launch_sym64<OP_LSL>(L, d0, acc, s); break;
+        }
+        if (L.sym[1].far) ctx->launches++;
     } else if (f32 && transposed) {
         KArgs<float> ka;
         ka.pos = L.pos32; ka.wn = L.wn32;

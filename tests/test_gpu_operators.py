@@ -129,8 +129,10 @@ def test_full_sphere_h32_bench_configuration(gpu_ctx):
 
 
 def test_large_ellipsoid_sampled_rows(gpu_ctx):
-    # h = 1/128 ellipsoid (1, 0.7, 0.5): N = 138830, 1.9e10 pairs per apply;
-    # the oracle evaluates 64 sampled targets of the double layers
+    # h = 1/128 ellipsoid (1, 0.7, 0.5): N = 138830, 1.9e10 pairs per apply,
+    # the launch configuration of the large workload (both precisions run
+    # their symmetric plans there); the oracle evaluates 64 sampled targets of
+    # each operator
     import torch
     import paper_2110_10749_gb300 as ssd
     p = Q.ellipsoid_points((1.0, 0.7, 0.5), 1 / 128)
@@ -141,12 +143,15 @@ def test_large_ellipsoid_sampled_rows(gpu_ctx):
     rows = np.random.default_rng(9).choice(n, 64, replace=False)
     P = ssd.Points.from_numpy(p).prepare(gpu_ctx)
     tg, tv = torch.as_tensor(g, device="cuda"), torch.as_tensor(v, device="cuda")
-    refL = oracle.laplace_dl(p, d, g, rows=rows)
-    refS = oracle.stokes_dl(p, d, v, rows=rows)
-    outL = ssd.laplace_DL(gpu_ctx, P, d, tg, ssd.FP32C).cpu().numpy()[rows]
-    outS = ssd.stokes_DL(gpu_ctx, P, d, tv, ssd.FP32C).cpu().numpy()[:, rows]
-    assert np.linalg.norm(outL - refL) / np.linalg.norm(refL) < 1e-5
-    assert np.linalg.norm(outS - refS) / np.linalg.norm(refS) < 1e-5
+    ref = {"LDL": oracle.laplace_dl(p, d, g, rows=rows), "SDL": oracle.stokes_dl(p, d, v, rows=rows),
+           "LSL": oracle.laplace_sl(p, d, g, targets=p["xyz"][:, rows]),
+           "SSL": oracle.stokes_sl(p, d, MU, v, targets=p["xyz"][:, rows])}
+    for prec, tol in ((ssd.FP32C, 1e-5), (ssd.FP64, 1e-12)):
+        out = {"LDL": ssd.laplace_DL(gpu_ctx, P, d, tg, prec), "SDL": ssd.stokes_DL(gpu_ctx, P, d, tv, prec),
+               "LSL": ssd.laplace_SL(gpu_ctx, P, d, tg, prec), "SSL": ssd.stokes_SL(gpu_ctx, P, d, MU, tv, prec)}
+        for k, b in ref.items():
+            a = out[k].cpu().numpy()[..., rows]
+            assert np.linalg.norm(a - b) / np.linalg.norm(b) < tol, (prec, k)
     P.release()
 
 
