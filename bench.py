@@ -74,8 +74,10 @@ FLOPS = {0: (11, 23), 1: (17, 29), 2: (26, 54), 3: (31, 50), 4: (51, 83), 5: (19
 KNAMES = ["laplace_SL", "laplace_DL", "stokes_SL", "stokes_DL", "stokes_SLDL", "laplace_SLDL"]
 # DRAM bytes (read + write) per launch of the dominant kernel on the headline
 # workload, from one ncu capture, keyed by kernel class; None when no capture
-# of the current kernel exists
-DRAM_BYTES = {}
+# of the current kernel exists.  Stokes DL on the symmetric plan: one
+# application is two launches, near/diagonal items 10.44 MB read and far block
+# pairs 10.36 MB read, nothing written to DRAM (the FP64 accumulator stays in L2)
+DRAM_BYTES = {3: 20.80e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -387,6 +389,13 @@ def run_ours(args):
     e1.synchronize()
     tts_ms = e0.elapsed_time(e1)
     tts_pairs = _pairs(ctx, ssd.FP32C) + _pairs(ctx, ssd.FP64)
+    # where the solve's pair-sum time goes, by operator and precision
+    tts_kernels = {}
+    for c in range(6):
+        for pname, pr in (("fp32c", ssd.FP32C), ("fp64", ssd.FP64)):
+            st = ctx.kernel_stats(c, pr)
+            if st["launches"]:
+                tts_kernels.setdefault(KNAMES[c], {})[pname] = {"launches": st["launches"], "ms": round(st["ms"], 1)}
     ctx.set_timing(False)
     inner = np.array(sol["inner_its"], dtype=np.int64).reshape(-1, 2)
     zq = sol["q"].clone()
@@ -397,11 +406,13 @@ def run_ours(args):
           "fp32c_time_to_solution_ms": tts_ms, "pairs": tts_pairs,
           "pairs_per_s": tts_pairs / (tts_ms / 1e3),
           "solve": "FP32C sweeps to an interface residual of 1e-6, then FP64-residual refinement to 1e-8 "
-                   "(each refinement step: one FP32C sweep, one plain-FP64 sweep started from it, one FP32C "
-                   "correction solve); pairs of both precisions counted",
+                   "(each refinement step: one FP32C sweep, then an FP64 sweep started from it whose local "
+                   "solves are themselves refined: FP64 residual, FP32C correction; then one FP32C "
+                   "correction solve of the interface system); pairs of both precisions counted",
           "local_gmres_steps": {"darcy": int(inner[:, 0].sum()), "stokes": int(inner[:, 1].sum()),
                                 "max_darcy": int(inner[:, 0].max()), "max_stokes": int(inner[:, 1].max())},
-          "drag": [float(v) for v in sol["drag"]]}
+          "drag": [float(v) for v in sol["drag"]],
+          "pair_kernels": tts_kernels}
 
     # timed steps: D-N sweeps from the converged state
     out5 = {k: torch.empty_like(v) for k, v in (("q", zq), ("p", zq), ("u", zu), ("f", zu))}
