@@ -338,9 +338,11 @@ typedef struct {
     ssd_krylov inner;          /* local solves; inner.tol applies to both */
     int refine;                /* FP32C interface GMRES only: up to this many refinement
                                   steps, each taking the true residual F(z) - z from one
-                                  plain-FP64 sweep and solving D (I - G) e = D r for the
-                                  correction with FP32C sweeps; the returned fields are
-                                  those of the last FP64 sweep.  0 = off */
+                                  FP64 sweep (whose local systems are solved by iterative
+                                  refinement: FP64 residual, FP32C correction) and solving
+                                  D (I - G) e = D r for the correction with FP32C sweeps;
+                                  the returned fields are those of the last FP64 sweep.
+                                  0 = off */
 } ssd_ddm_params;
 
 /*
