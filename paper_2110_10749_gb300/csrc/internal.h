@@ -92,7 +92,7 @@ struct ssd_ctx {
     int occ32 = 1, occ64 = 1;  // resident CTAs per SM of the pair kernels
     int waves32 = 12;          // FP32C grid: about this many waves of resident CTAs (tuned)
     int lpt = 1;               // pair grids in near-first order on prepared layouts
-    int sym = 1;               // FP32C double layers: far block pairs once for both directions
+    int sym = 1;               // layer operators (both precisions): far block pairs once for both directions
     int waves64 = 8;           // FP64 grid: about this many waves of resident CTAs (tuned)
     void *noalloc_scratch = nullptr;   // device address of the no-alloc scratch array (first no-alloc call)
     std::string err;
