@@ -76,8 +76,8 @@ KNAMES = ["laplace_SL", "laplace_DL", "stokes_SL", "stokes_DL", "stokes_SLDL", "
 # workload, from one ncu capture, keyed by kernel class; None when no capture
 # of the current kernel exists.  Stokes DL on the symmetric plan: one
 # application is two launches, near/diagonal items 10.44 MB read and far block
-# pairs 10.36 MB read, nothing written to DRAM (the FP64 accumulator stays in L2)
-DRAM_BYTES = {3: 20.80e6}
+# pairs 10.32 MB read, nothing written to DRAM (the FP64 accumulator stays in L2)
+DRAM_BYTES = {3: 20.76e6}
 L2_FLUSH_BYTES = 256 << 20
 
 

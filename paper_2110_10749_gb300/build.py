@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj, r.stdout + r.stderr
 
     # tile-shape overrides for tuning sweeps (see csrc/internal.h)
-    for key in ("SSD_TPB32", "SSD_MINCTA32", "SSD_TPT32"):
+    for key in ("SSD_TPB32", "SSD_MINCTA32", "SSD_TPT32", "SSD_SYMTPT", "SSD_SYMMINCTA"):
         if os.environ.get(key):
             FLAGS_EXTRA.append("-D%s=%d" % (key, int(os.environ[key])))
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:

@@ -25,6 +25,10 @@ constexpr int kMinCTA32 = SSD_MINCTA32;   // resident CTAs per SM the FP32C kern
 #define SSD_TPT32 4
 #endif
 constexpr int kTPT32 = SSD_TPT32;   // targets per thread, FP32C (pairs of packed f32x2 lanes)
+#ifndef SSD_SYMTPT
+#define SSD_SYMTPT 8
+#endif
+constexpr int kSymTPT = SSD_SYMTPT; // targets per thread of the FP32C symmetric kernel (4 or 8)
 constexpr int kChunk = 32;          // sources per bounding-box chunk (near/far test per warp)
 constexpr int kTPB64 = 128;         // threads per CTA, FP64 pair kernel
 constexpr int kTPT64 = 1;           // targets per thread, FP64

@@ -36,6 +36,21 @@ constexpr double kRhoFar64 = 8.0;    // 1 - s_i(rho) < 1e-21 beyond this (FP64)
 // a divisor of n_pad), far items of at most kSymTiles source tiles
 constexpr int kSymBlock = kTPB32 * kTPT32;
 constexpr int kSymTiles = 8;
+// FP32C symmetric kernel: threads per CTA and resident CTAs per SM for its
+// targets per thread (4: 128 threads, as the direct kernel; 8: 64 threads).
+// With 8 targets the Stokes layers keep every value in registers at 4
+// resident CTAs (up to 255 registers); the Laplace layers fit 6 (measured at
+// N = 138830: Stokes DL 11.5 ms at 4 against 12.1 ms at 6, where it spills;
+// Laplace DL 7.55 ms at 6 against 7.72 ms at 4)
+constexpr int kSymTPB32 = kSymBlock / kSymTPT;
+constexpr int sym_min_cta(int op) {
+#ifdef SSD_SYMMINCTA
+    return op >= 0 ? SSD_SYMMINCTA : 0;
+#else
+    return kSymTPT == 4 ? kMinCTA32 : ((op == OP_SDL || op == OP_SSL) ? 4 : 6);
+#endif
+}
+static_assert(kSymTPB32 % 32 == 0 && kSymTPT % 2 == 0, "whole warps and packed target pairs");
 
 template <int OP> struct OpInfo;
 template <> struct OpInfo<OP_LSL>   { enum { NC = 1, WN = 0, D1 = 0, SL = 1, DL = 0 }; };
@@ -683,11 +698,13 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) pair32_kernel(const K32Args
 //               a <- S(yh) (w f)_b,     b <- S(yh) (w f)_a
 // (the reverse terms follow from yh -> -yh and swapping the roles), so r, its
 // powers and the density difference are shared by both directions.
-// A CTA holds 512 targets (4 per thread) of one block and walks source tiles
+// A CTA holds the 512 targets of one block (kSymTPT per thread as packed
+// f32x2 pairs: 8 per thread in 64 threads by default) and walks source tiles
 // of 128 staged in shared memory.  At step s lane l takes source
 // (l + s) mod 128, so the 32 lanes of a warp work on 32 different sources and
 // add their reverse terms to the warp's own shared accumulator without
-// conflict; after the tile the four warps' accumulators are summed.  Forward
+// conflict; after the tile the warps' accumulators are summed.  More targets
+// per thread share each staged source and each reverse-sum update.  Forward
 // sums fold per tile into (hi, lo) pairs; both directions end in an FP64
 // atomic add to acc[c][point].
 struct SymItem {
@@ -702,11 +719,12 @@ struct SymArgs {
 };
 
 template <int OP>
-__global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs a) {
+__global__ void __launch_bounds__(kSymTPB32, sym_min_cta(OP)) sym32_kernel(const SymArgs a) {
     constexpr int NC = OpInfo<OP>::NC;
-    constexpr int NP = kTPT32 / 2;
-    constexpr int NW = kTPB32 / 32;
-    static_assert(kTile == kTPB32, "one staged source per thread");
+    constexpr int TPB = kSymTPB32;
+    constexpr int NP = kSymTPT / 2;
+    constexpr int NW = TPB / 32;
+    static_assert(kTile % TPB == 0, "whole staged sources per thread");
     // source records packed for the step loop: (x, y, z, d0.x), (w n, d0.y), d0.z;
     // reverse sums one float per component, warp and source
     __shared__ float4 sm_a[kTile], sm_b[kTile];
@@ -717,7 +735,7 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
     float2 y[NP][3], dt[NP][3], tm[NP][3];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        const int64_t i0 = it.tb + threadIdx.x + (2 * k) * kTPB32, i1 = i0 + kTPB32;
+        const int64_t i0 = it.tb + threadIdx.x + (2 * k) * TPB, i1 = i0 + TPB;
         const float4 p0 = a.pos[i0], p1 = a.pos[i1];
         const float4 e0 = a.d0[i0], e1 = a.d0[i1];
         const float4 m0 = a.wn[i0], m1 = a.wn[i1];
@@ -725,24 +743,25 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
         dt[k][0] = make_float2(e0.x, e1.x); dt[k][1] = make_float2(e0.y, e1.y); dt[k][2] = make_float2(e0.z, e1.z);
         tm[k][0] = make_float2(m0.x, m1.x); tm[k][1] = make_float2(m0.y, m1.y); tm[k][2] = make_float2(m0.z, m1.z);
     }
-    float hi[kTPT32][NC], lo[kTPT32][NC];
+    float hi[kSymTPT][NC], lo[kSymTPT][NC];
 #pragma unroll
-    for (int t = 0; t < kTPT32; ++t)
+    for (int t = 0; t < kSymTPT; ++t)
 #pragma unroll
         for (int q = 0; q < NC; ++q) hi[t][q] = lo[t][q] = 0.f;
 
     for (int64_t tile = it.s0; tile < it.s1; tile += kTile) {
         __syncthreads();
-        {
-            const float4 ps = a.pos[tile + threadIdx.x], ms = a.wn[tile + threadIdx.x], ds = a.d0[tile + threadIdx.x];
-            sm_a[threadIdx.x] = make_float4(ps.x, ps.y, ps.z, ds.x);
-            sm_b[threadIdx.x] = make_float4(ms.x, ms.y, ms.z, ds.y);
-            if (NC == 3) sm_c[threadIdx.x] = ds.z;
+#pragma unroll
+        for (int js = threadIdx.x; js < kTile; js += TPB) {
+            const float4 ps = a.pos[tile + js], ms = a.wn[tile + js], ds = a.d0[tile + js];
+            sm_a[js] = make_float4(ps.x, ps.y, ps.z, ds.x);
+            sm_b[js] = make_float4(ms.x, ms.y, ms.z, ds.y);
+            if (NC == 3) sm_c[js] = ds.z;
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sm_rev[q][w][js] = 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < NC; ++q)
-#pragma unroll
-            for (int w = 0; w < NW; ++w) sm_rev[q][w][threadIdx.x] = 0.f;
         __syncthreads();
         float2 part[NP][NC];
 #pragma unroll
@@ -816,20 +835,22 @@ __global__ void __launch_bounds__(kTPB32, kMinCTA32) sym32_kernel(const SymArgs 
                     lo[t][q] += (hi[t][q] - (sum - bp)) + (p - bp);
                     hi[t][q] = sum;
                 }
-        // reverse: the four warps' sums of source tile + threadIdx.x
+        // reverse: the warps' sums of each source of the tile
         __syncthreads();
-        const int64_t jb = tile + threadIdx.x;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            float r = sm_rev[q][0][threadIdx.x];
+        for (int js = threadIdx.x; js < kTile; js += TPB) {
 #pragma unroll
-            for (int w = 1; w < NW; ++w) r += sm_rev[q][w][threadIdx.x];
-            atomicAdd(a.acc + q * a.n_pad + jb, (double)r);
+            for (int q = 0; q < NC; ++q) {
+                float r = sm_rev[q][0][js];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) r += sm_rev[q][w][js];
+                atomicAdd(a.acc + q * a.n_pad + tile + js, (double)r);
+            }
         }
     }
 #pragma unroll
-    for (int t = 0; t < kTPT32; ++t) {
-        const int64_t i = it.tb + threadIdx.x + t * kTPB32;
+    for (int t = 0; t < kSymTPT; ++t) {
+        const int64_t i = it.tb + threadIdx.x + t * TPB;
 #pragma unroll
         for (int q = 0; q < NC; ++q) atomicAdd(a.acc + q * a.n_pad + i, (double)hi[t][q] + (double)lo[t][q]);
     }
@@ -1546,7 +1567,7 @@ cudaError_t launch_sym(const Layout &L, const float4 *d0, double *acc, cudaStrea
     sa.pos = L.pos32; sa.wn = L.wn32; sa.d0 = d0;
     sa.items = reinterpret_cast<const SymItem *>(b + o_far);
     sa.n_pad = L.n_pad; sa.acc = acc;
-    sym32_kernel<OP><<<(unsigned)pl.far, kTPB32, 0, s>>>(sa);
+    sym32_kernel<OP><<<(unsigned)pl.far, kSymTPB32, 0, s>>>(sa);
     return cudaGetLastError();
 }
 
