@@ -61,7 +61,20 @@ enum ssd_precision { SSD_FP64 = 0, SSD_FP32C = 1 };
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device` (which becomes current for the
- * calling thread).  *ctx receives the handle. */
+ * calling thread).  *ctx receives the handle.
+ *
+ * Tuning read from the environment at creation (all optional):
+ *   SSD_PAIR_SYM=0      no symmetric far-block plans: every operator on a
+ *                       prepared layout runs the direct kernels, whose split
+ *                       sums are added in a fixed order (results reproducible
+ *                       bit for bit); with the plans (default) the far block
+ *                       pairs of the four layer operators are evaluated once
+ *                       for both directions and summed by FP64 atomic adds,
+ *                       so results vary in the last bits of an FP64 sum
+ *   SSD_PAIR_LPT=0      direct FP32C/FP64 grids in plain (tile, split) order
+ *                       instead of near-first order
+ *   SSD_PAIR_WAVES=k    FP32C direct grid sized for k (1..64) waves of resident CTAs
+ *   SSD_PAIR_WAVES64=k  the same for the FP64 direct grid */
 int ssd_ctx_create(ssd_ctx **ctx, int device);
 /* Free the context, its workspace and layouts.  NULL is accepted. */
 int ssd_ctx_destroy(ssd_ctx *ctx);
