@@ -248,7 +248,11 @@ int ssd_stokes_DL_noalloc(ssd_ctx *ctx, const ssd_points *pts, double delta, con
  * ssd_points_prepare builds, or an equal temporary one): row k is caller
  * point order[k] of ssd_points_order.  Computes out[c][order[k]] for
  * row_begin <= k < row_end only (the other entries of out are not written),
- * bit-identical to the same entries of the whole application.  op: 0 = L
+ * with the direct kernels and the whole application's splits, so bit-identical
+ * to the same entries of the whole application whenever that runs the direct
+ * kernels too (SSD_PAIR_SYM=0, or a layout below the symmetric plans' share of
+ * far block pairs); where the whole application runs a symmetric plan the two
+ * agree to the rounding of the precision.  op: 0 = L
  * (ssd_laplace_SL), 1 = D^L (ssd_laplace_DL), 2 = M (ssd_stokes_SL, mu
  * used), 3 = D^S (ssd_stokes_DL); dens, out as for that call.  SSD_EINVAL
  * unless 0 <= row_begin < row_end <= n.  Asynchronous on `stream`. */

@@ -7,8 +7,9 @@ Two partitions of the work, both exact:
   block of the spatial (layout) order with ``ssd_apply_rows``, and one
   all-reduce of the zero-filled results assembles the application on every
   rank (adding zeros is exact, so the result is bit-identical to the
-  one-device application).  Compute is O(N^2 / P) per rank against O(N)
-  exchanged.
+  one-device application on the direct kernels, and equal to the rounding
+  of the precision where the one-device application runs a symmetric
+  plan).  Compute is O(N^2 / P) per rank against O(N) exchanged.
 * Surfaces of a batch.  Independent problems: each rank takes a set of
   surfaces, balanced by their pair counts, and nothing is exchanged until the
   results are gathered.
