@@ -104,6 +104,13 @@ int ssd_ctx_reset_stats(ssd_ctx *ctx);
 /* Total kernel launches the library issued since the context was created
  * (every kernel of the library, not only the pair sums). */
 int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out /* host */);
+/* Wait for the work queued on `stream` (on the whole device when stream is
+ * NULL) and report failures of asynchronous calls: the operator, row-block,
+ * batched-application and field calls return once their kernels are queued,
+ * so a kernel that fails there surfaces here as SSD_ECUDA (SSD_ENOMEM for an
+ * allocation), with the CUDA error text in ssd_ctx_last_error.  SSD_EINVAL
+ * when the calling thread's current device is not the context's. */
+int ssd_sync(ssd_ctx *ctx, ssd_stream stream);
 /* Measurement aid (the paper has no counterpart): the FP32 FMA rate this
  * device reaches, in TFLOP/s (FMA = 2 flops), from a kernel that keeps 16
  * independent FMA chains per thread on every SM (packed = 1: as f32x2

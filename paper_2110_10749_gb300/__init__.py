@@ -32,7 +32,7 @@ K_LAPLACE_SL, K_LAPLACE_DL, K_STOKES_SL, K_STOKES_DL, K_STOKES_SLDL, K_LAPLACE_S
 # Every entry point declared in include/ssd.h.
 EXPORTS = [
     "ssd_ctx_create", "ssd_ctx_destroy", "ssd_status_string", "ssd_ctx_last_error",
-    "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count",
+    "ssd_ctx_set_timing", "ssd_ctx_kernel_stats", "ssd_ctx_reset_stats", "ssd_ctx_launch_count", "ssd_sync",
     "ssd_fp32_fma_rate",
     "ssd_quadrature_points", "ssd_quadrature_jacobian", "ssd_points_prepare", "ssd_points_release",
     "ssd_laplace_SL", "ssd_laplace_DL", "ssd_stokes_SL", "ssd_stokes_DL",
@@ -125,6 +125,7 @@ def lib():
         "ssd_ctx_kernel_stats": [P, i, i, C.POINTER(CKernelStats)],
         "ssd_ctx_reset_stats": [P],
         "ssd_ctx_launch_count": [P, C.POINTER(i64)],
+        "ssd_sync": [P, P],
         "ssd_fp32_fma_rate": [P, i, C.POINTER(d)],
         "ssd_quadrature_points": [P, C.POINTER(CSurface), d, d, i64, C.POINTER(i64), P, P, P, P, P],
         "ssd_quadrature_jacobian": [P, C.POINTER(CSurface), d, d, i64, P, P, P, P],
@@ -270,6 +271,11 @@ class Context:
         v = C.c_int64()
         self.check(lib().ssd_ctx_launch_count(self.h, C.byref(v)), "ssd_ctx_launch_count")
         return v.value
+
+    def sync(self, device_wide=False):
+        """ssd_sync on torch's current stream (or the whole device): raises
+        SsdError if a kernel of an asynchronous call failed."""
+        self.check(lib().ssd_sync(self.h, None if device_wide else _stream()), "ssd_sync")
 
 
 class Points:

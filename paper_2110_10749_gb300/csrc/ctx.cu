@@ -683,6 +683,15 @@ int ssd_ctx_launch_count(const ssd_ctx *ctx, int64_t *out) {
     return SSD_OK;
 }
 
+int ssd_sync(ssd_ctx *ctx, ssd_stream stream) {
+    if (!ctx) return SSD_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device)
+        return set_error(ctx, SSD_EINVAL, "the current device is not the context's device");
+    const cudaError_t e = stream ? cudaStreamSynchronize((cudaStream_t)stream) : cudaDeviceSynchronize();
+    return cuda_check(ctx, e, "synchronise");
+}
+
 int ssd_points_prepare(ssd_ctx *ctx, ssd_points *pts, ssd_stream stream) {
     if (!ctx) return SSD_EINVAL;
     if (pts && pts->layout) return set_error(ctx, SSD_EINVAL, "points already have a layout");

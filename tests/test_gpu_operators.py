@@ -169,3 +169,18 @@ def test_invalid_arguments(gpu_ctx):
         ssd.stokes_SL(gpu_ctx, P, 0.5, -1.0, torch.zeros((3, p["w"].size), dtype=torch.float64, device="cuda"))
     with pytest.raises(ssd.SsdError):
         ssd.laplace_DL(gpu_ctx, P, 0.5, g, prec=7)
+
+
+def test_sync_after_asynchronous_calls(gpu_ctx):
+    # operator calls return once queued; ssd_sync waits for them on the
+    # stream (or the device) and reports success when the kernels ran
+    import torch
+    import paper_2110_10749_gb300 as ssd
+    p = Q.sphere_points(1.0, 1 / 8)
+    P = ssd.Points.from_numpy(p)
+    g = torch.ones(p["w"].size, dtype=torch.float64, device="cuda")
+    out = ssd.laplace_DL(gpu_ctx, P, 3 / 8, g, ssd.FP32C)
+    gpu_ctx.sync()
+    gpu_ctx.sync(device_wide=True)
+    # the double layer of a constant vanishes (subtracted form, eq. H_subtr)
+    assert float(out.abs().max()) < 1e-12
